@@ -1,0 +1,104 @@
+"""Ideal MHD fluxes (Eq. 2.2), the 1D HLL Riemann solver and the multidimensional
+edge electric field -- oracle version.
+
+Units: rationalised (Heaviside-Lorentz): the Gaussian factors 1/(4 pi) and
+1/(8 pi) of Eq. 2.2 become 1 and 1/2; B_G = sqrt(4 pi) B_HL.  Conserved
+variables U = (rho, rho v, eps, B) with eps = rho v^2/2 + P/(gamma-1) + B^2/2.
+
+Readings (the paper does not name its solvers):
+  * 1D Riemann solver at face points (Sec. VI step 5): HLL with Davis wave speeds
+    S_L = min(vn_L - cf_L, vn_R - cf_R), S_R = max(vn_L + cf_L, vn_R + cf_R),
+    cf the fast magnetosonic speed along the unit normal; all 8 components.
+  * Multidimensional Riemann solver at edge points (MuSIC in the paper): a
+    multidimensional Rusanov electric field for the k zones around an edge with
+    unit tangent t,
+      E.t = (1/k) [ sum_z (-v_z x B_z).t + sum_f a_f (B_R(f) - B_L(f)).(t x n_f) ],
+    a_f = max(|vn| + cf) of the two states of face f along its unit normal n_f.
+    It reduces to the 2D Rusanov/UCT field on an orthogonal 4-zone edge and to
+    -v x B for identical states.
+
+Pinned by: tests/test_oracle_physics.py -- consistency (identical states give the
+exact flux / -v x B), rotational invariance, HLL equal to upwind flux for
+supersonic states, the 4-zone Cartesian reduction to 1D Rusanov induction.
+"""
+import numpy as np
+
+RHO, MX, MY, MZ, EN, BX, BY, BZ = range(8)
+
+
+def primitives(U, gamma):
+    rho = U[..., RHO]
+    v = U[..., MX:MZ + 1] / rho[..., None]
+    B = U[..., BX:BZ + 1]
+    p = (gamma - 1.0) * (U[..., EN] - 0.5 * rho * (v * v).sum(-1) - 0.5 * (B * B).sum(-1))
+    return rho, v, p, B
+
+
+def conserved(rho, v, p, B, gamma):
+    U = np.zeros(np.shape(rho) + (8,))
+    U[..., RHO] = rho
+    U[..., MX:MZ + 1] = rho[..., None] * v
+    U[..., EN] = p / (gamma - 1.0) + 0.5 * rho * (v * v).sum(-1) + 0.5 * (B * B).sum(-1)
+    U[..., BX:BZ + 1] = B
+    return U
+
+
+def flux_dir(U, nvec, gamma):
+    """Physical flux F(U).n for an arbitrary (not necessarily unit) vector n."""
+    rho, v, p, B = primitives(U, gamma)
+    vn = (v * nvec).sum(-1)
+    Bn = (B * nvec).sum(-1)
+    pt = p + 0.5 * (B * B).sum(-1)
+    vB = (v * B).sum(-1)
+    F = np.empty(U.shape)
+    F[..., RHO] = rho * vn
+    F[..., MX:MZ + 1] = rho[..., None] * v * vn[..., None] + pt[..., None] * nvec - B * Bn[..., None]
+    F[..., EN] = (U[..., EN] + pt) * vn - Bn * vB
+    F[..., BX:BZ + 1] = B * vn[..., None] - v * Bn[..., None]
+    return F
+
+
+def fast_speed(U, nhat, gamma):
+    rho, v, p, B = primitives(U, gamma)
+    a2 = gamma * p / rho
+    b2 = (B * B).sum(-1) / rho
+    bn2 = (B * nhat).sum(-1) ** 2 / rho
+    s = a2 + b2
+    return np.sqrt(0.5 * (s + np.sqrt(np.maximum(s * s - 4.0 * a2 * bn2, 0.0))))
+
+
+def hll(UL, UR, nhat, gamma):
+    """HLL flux along the unit normal nhat."""
+    vnL = (UL[..., MX:MZ + 1] * nhat).sum(-1) / UL[..., RHO]
+    vnR = (UR[..., MX:MZ + 1] * nhat).sum(-1) / UR[..., RHO]
+    cL = fast_speed(UL, nhat, gamma)
+    cR = fast_speed(UR, nhat, gamma)
+    SL = np.minimum(vnL - cL, vnR - cR)
+    SR = np.maximum(vnL + cL, vnR + cR)
+    FL = flux_dir(UL, nhat, gamma)
+    FR = flux_dir(UR, nhat, gamma)
+    Fs = (SR[..., None] * FL - SL[..., None] * FR
+          + (SL * SR)[..., None] * (UR - UL)) / (SR - SL)[..., None]
+    out = np.where((SL >= 0.0)[..., None], FL, np.where((SR <= 0.0)[..., None], FR, Fs))
+    return out
+
+
+def rusanov_speed(U, nhat, gamma):
+    vn = (U[..., MX:MZ + 1] * nhat).sum(-1) / U[..., RHO]
+    return np.abs(vn) + fast_speed(U, nhat, gamma)
+
+
+def edge_emf(states, faces, tvec, gamma):
+    """Multidimensional Rusanov E.t at one edge point.
+
+    states: (k, 8) zone states; faces: list of (iL, iR, nhat(3,)); tvec unit tangent."""
+    k = states.shape[0]
+    rho = states[:, RHO]
+    v = states[:, MX:MZ + 1] / rho[:, None]
+    B = states[:, BX:BZ + 1]
+    E = -np.cross(v, B)
+    acc = (E @ tvec).sum()
+    for iL, iR, nh in faces:
+        a = max(rusanov_speed(states[iL], nh, gamma), rusanov_speed(states[iR], nh, gamma))
+        acc += a * np.dot(B[iR] - B[iL], np.cross(tvec, nh))
+    return acc / k

@@ -1,0 +1,231 @@
+"""WENO-AO reconstruction in the Taylor basis (Sec. III, Eqs. 3.1-3.4) -- oracle.
+
+The paper sketches WENO-AO and defers its details to Balsara et al. 2018/2019,
+which are not available.  Readings (the GPU path implements the same ones):
+  * Basis: Taylor basis of zone 0 (Eq. 3.1): 1 and phi_m = s^m - <s^m>_0 for every
+    monomial m of degree 1..p-1 in s = (x - x_0)/l_0, centroid x_0 (Eq. 3.3),
+    l_0 = V_0^(1/3).
+  * Fit conditions (Eq. 3.4, "reconstruction by primitive"): the volume average of
+    the polynomial over stencil zone j equals its zone average; written directly
+    as sum_m u_m <phi_m>_j = u_j - u_0 with <phi_m>_j integrated by cubature over
+    zone j (the parallel-axis form of Eq. 3.4 is the same number).
+  * Stencils by mesh adjacency (so seams and cube corners need no special case):
+      central  p=2: the 6 face neighbours; p=3: every zone sharing a vertex with
+               zone 0 (<= 26); p=4: that set plus the zones two steps away along
+               each logical axis (<= 32).  Least squares (Sec. III).
+      small    8 "octant" stencils {0, one face neighbour per logical axis with
+               signs s in {+-}^3}, exactly determined linear fits (the CWENO-type
+               small stencils of Sec. III).
+  * Smoothness: beta = sum_{1<=|a|<=p-1} <(d^a_s P)^2>_0, each multi-index a once.
+  * AO combination (Balsara, Garain & Shu 2016 family):
+      P = (w_H/g_H)(P_H - sum_k g_k P_k) + sum_k w_k P_k,
+    g_H = 0.85, g_k = 0.15/8, w_m = g_m/(beta_m + eps)^2 normalised, eps = 1e-12.
+  * Variables: all eight conserved components, componentwise (Sec. VI step 2).
+  * Boundaries: ghost zones continue the log shells (geometry); their data are
+    copies of the boundary shell (continuative outflow, Sec. VII).
+
+Pinned by: tests/test_oracle_weno.py -- constants reproduced exactly; linear data
+reproduced exactly for every p; the central least-squares fit reproduces every
+polynomial of degree <= p-1 exactly on the curved mapped zones; smoothness of the
+central stencil equals the analytic integral for a known polynomial.
+parity unpinned (only by invariants): the constants g_H, g_k, eps and the
+stencil choices are readings, not values the paper fixes.
+"""
+import itertools
+
+import numpy as np
+
+from .mesh import taylor_exponents
+
+GAMMA_H = 0.85
+GAMMA_K = 0.15 / 8.0
+EPS = 1e-12
+
+# local face -> side index (s, e, n, w) of the column
+LF_SIDE = {0: 3, 1: 1, 2: 0, 3: 2}
+
+
+def ghost_layers(p):
+    return 2 if p == 4 else 1
+
+
+class Stencils:
+    """Stencils of every zone as lists of (column, shell) pairs; shells may be ghosts."""
+
+    def __init__(self, mesh):
+        m = mesh
+        self.mesh = m
+        p = m.p
+        self.angular_nb = np.zeros((m.ncol, 4), dtype=np.int64)   # by local face 0..3
+        for c in range(m.ncol):
+            for lf in range(4):
+                se = m.col_edges[c, LF_SIDE[lf]]
+                a, b = m.se_L[se], m.se_R[se]
+                self.angular_nb[c, lf] = b if a == c else a
+        self.central = []
+        self.octants = []
+        for c in range(m.ncol):
+            for k in range(m.nr):
+                self.central.append(self._central(c, k, p))
+                self.octants.append(self._octants(c, k))
+
+    def face_nb(self, c, k, lf):
+        if lf < 4:
+            return (self.angular_nb[c, lf], k)
+        return (c, k - 1) if lf == 4 else (c, k + 1)
+
+    def _octants(self, c, k):
+        out = []
+        for oz, oy, ox in itertools.product((0, 1), repeat=3):
+            out.append([self.face_nb(c, k, ox), self.face_nb(c, k, 2 + oy),
+                        self.face_nb(c, k, 4 + oz)])
+        return out            # order o = ox + 2 oy + 4 oz
+
+    def _central(self, c, k, p):
+        m = self.mesh
+        if p == 2:
+            return sorted(self.face_nb(c, k, lf) for lf in range(6))
+        cols = set()
+        for v in m.col_verts[c]:
+            cols.update(m.sv_cols[v])
+        st = set()
+        for cc in cols:
+            for dk in (-1, 0, 1):
+                st.add((cc, k + dk))
+        st.discard((c, k))
+        if p == 4:
+            st.add((c, k - 2))
+            st.add((c, k + 2))
+            for lf in range(4):
+                c1 = self.angular_nb[c, lf]
+                se = m.col_edges[c, LF_SIDE[lf]]
+                s1 = list(m.col_edges[c1]).index(se)
+                se2 = m.col_edges[c1, (s1 + 2) % 4]
+                a, b = m.se_L[se2], m.se_R[se2]
+                st.add((b if a == c1 else a, k))
+        return sorted(st)
+
+
+def smoothness_matrix(s, dV, V, exps, p):
+    """Q[m, m'] = sum_{1<=|a|<=p-1} <d^a s^m d^a s^m'>_0 from cubature points s (nz, np, 3)."""
+    nz = s.shape[0]
+    ne = len(exps)
+    Q = np.zeros((nz, ne, ne))
+    for order in range(1, p):
+        for a in taylor_exponents(order, order):
+            d = np.zeros(s.shape[:2] + (ne,))
+            for j, e in enumerate(exps):
+                if np.any(e < a):
+                    continue
+                coef = 1.0
+                for ax in range(3):
+                    for t in range(a[ax]):
+                        coef *= (e[ax] - t)
+                r = e - a
+                d[:, :, j] = coef * s[..., 0] ** r[0] * s[..., 1] ** r[1] * s[..., 2] ** r[2]
+            Q += np.einsum("zp,zpi,zpj->zij", dV, d, d) / V[:, None, None]
+    return Q
+
+
+class WenoAO:
+    """Per-zone WENO-AO tables built directly from each zone's geometry."""
+
+    def __init__(self, mesh):
+        m = self.mesh = mesh
+        p = m.p
+        self.g = ghost_layers(p)
+        self.exps = taylor_exponents(p - 1)          # degree 1..p-1
+        self.nc1 = len(self.exps)
+        st = self.st = Stencils(m)
+        nre = m.nr + 2 * self.g
+        cext = np.repeat(np.arange(m.ncol), nre)
+        kext = np.tile(np.arange(-self.g, m.nr + self.g), m.ncol)
+        self.geo_ext = m.zone_geometry(cext, kext)
+        self.nre = nre
+
+        def ext(ck):
+            return ck[0] * nre + ck[1] + self.g
+
+        Z = m.Z
+        zc = np.repeat(np.arange(m.ncol), m.nr)
+        zk = np.tile(np.arange(m.nr), m.ncol)
+        self.zext = zc * nre + zk + self.g
+        g0 = {key: self.geo_ext[key][self.zext] for key in ("V", "xc", "l0", "xg", "dV")}
+        self.geo0 = g0
+        # Taylor-basis means over zone 0 (the constants of Eq. 3.1)
+        self.mean0 = m.scaled_moments(g0, g0["xc"], g0["l0"], self.exps)
+        nmax = max(len(s) for s in st.central)
+        self.nmax = nmax
+        self.cidx = np.zeros((Z, nmax), dtype=np.int64)   # ext index of stencil zone
+        A = np.zeros((Z, nmax, self.nc1))
+        for z in range(Z):
+            for j, ck in enumerate(st.central[z]):
+                self.cidx[z, j] = ext(ck)
+            for j in range(len(st.central[z]), nmax):
+                self.cidx[z, j] = self.zext[z]               # padding row: zone 0 itself
+        for j in range(nmax):
+            gj = {key: self.geo_ext[key][self.cidx[:, j]] for key in ("V", "xg", "dV")}
+            Aj = m.scaled_moments(gj, g0["xc"], g0["l0"], self.exps) - self.mean0
+            real = np.array([j < len(st.central[z]) for z in range(Z)])
+            A[:, j, :] = np.where(real[:, None], Aj, 0.0)
+        self.A_central = A
+        self.pinv_central = np.linalg.pinv(A)               # (Z, nc1, nmax)
+        # octant stencils: linear fits on the three neighbours
+        lin = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]])
+        self.oidx = np.zeros((Z, 8, 3), dtype=np.int64)
+        for z in range(Z):
+            for o in range(8):
+                for q in range(3):
+                    self.oidx[z, o, q] = ext(st.octants[z][o][q])
+        self.inv_oct = np.zeros((Z, 8, 3, 3))
+        for o in range(8):
+            rows = []
+            for q in range(3):
+                gj = {key: self.geo_ext[key][self.oidx[:, o, q]] for key in ("V", "xg", "dV")}
+                rows.append(m.scaled_moments(gj, g0["xc"], g0["l0"], lin))
+            self.inv_oct[:, o] = np.linalg.inv(np.stack(rows, axis=1))
+        s = (g0["xg"] - g0["xc"][:, None, :]) / g0["l0"][:, None, None]
+        self.Q = smoothness_matrix(s, g0["dV"], g0["V"], self.exps, p)
+        # position of the linear monomials inside exps (they come first)
+        assert tuple(map(tuple, self.exps[:3])) == ((1, 0, 0), (0, 1, 0), (0, 0, 1))
+
+    def ext_data(self, U):
+        """Zone data on the extended (ghosted) index: ghosts copy the boundary shell."""
+        m = self.mesh
+        Uc = U.reshape(m.ncol, m.nr, -1)
+        kk = np.clip(np.arange(-self.g, m.nr + self.g), 0, m.nr - 1)
+        return Uc[:, kk, :].reshape(m.ncol * self.nre, -1)
+
+    def reconstruct(self, U, return_parts=False):
+        """Taylor coefficients (Z, 8, nc1) of the WENO-AO polynomial of every
+        conserved variable (the mean is the zone average itself)."""
+        Ue = self.ext_data(U)
+        u0 = U[:, None, :]
+        dH = Ue[self.cidx] - u0                                   # (Z, nmax, 8)
+        uH = np.einsum("zcj,zjv->zvc", self.pinv_central, dH)     # (Z, 8, nc1)
+        dO = Ue[self.oidx] - U[:, None, None, :]                  # (Z, 8, 3, 8)
+        uK = np.einsum("zoij,zojv->zovi", self.inv_oct, dO)       # (Z, 8oct, 8var, 3)
+        bH = np.einsum("zvc,zcd,zvd->zv", uH, self.Q, uH)
+        bK = (uK * uK).sum(-1)                                    # (Z, 8oct, 8var)
+        wH = GAMMA_H / (bH + EPS) ** 2
+        wK = GAMMA_K / (bK + EPS) ** 2
+        tot = wH + wK.sum(1)
+        wH = wH / tot
+        wK = wK / tot[:, None, :]
+        out = (wH / GAMMA_H)[..., None] * uH
+        lin = uH[..., :3] - GAMMA_K * uK.sum(1)
+        out[..., :3] = (wH / GAMMA_H)[..., None] * lin + (wK[..., None] * uK).sum(1)
+        if return_parts:
+            return out, dict(uH=uH, uK=uK, bH=bH, bK=bK, wH=wH, wK=wK)
+        return out
+
+    def evaluate(self, coeffs, U, pts):
+        """Value of the reconstructed polynomial at physical points pts (Z, np, 3)
+        -> (Z, np, 8)."""
+        g0 = self.geo0
+        s = (pts - g0["xc"][:, None, :]) / g0["l0"][:, None, None]
+        phi = np.ones(s.shape[:2] + (self.nc1,))
+        for d in range(3):
+            phi *= s[..., d:d + 1] ** self.exps[None, None, :, d]
+        phi -= self.mean0[:, None, :]
+        return U[:, None, :] + np.einsum("zpc,zvc->zpv", phi, coeffs)

@@ -1,0 +1,102 @@
+"""Pins of the oracle's WENO-AO reconstruction (Sec. III, Eqs. 3.1-3.4)."""
+import numpy as np
+import pytest
+
+from oracle import mesh as M
+from oracle import weno as W
+from oracle.mesh import taylor_exponents
+
+
+@pytest.fixture(scope="module", params=[2, 3, 4])
+def case(request):
+    p = request.param
+    m = M.Mesh(3, 5 if p == 4 else 4, 1.0, 2.0, p)
+    return m, W.WenoAO(m)
+
+
+def averages(w, f):
+    g = w.geo_ext
+    return np.einsum("zp,zp->z", g["dV"], f(g["xg"])) / g["V"]
+
+
+def interior(m, g):
+    k = np.arange(m.Z) % m.nr
+    return (k >= g) & (k < m.nr - g)
+
+
+def test_constants_exact(case):
+    m, w = case
+    U = np.tile(np.array([1.3, 0.2, -0.1, 0.4, 2.0, 0.5, -0.3, 0.7]), (m.Z, 1))
+    assert np.abs(w.reconstruct(U)).max() < 1e-13
+
+
+def test_linear_data_exact_for_every_order(case):
+    m, w = case
+    lin = lambda x: 0.3 + x[..., 0] - 2.0 * x[..., 1] + 0.5 * x[..., 2]
+    avg = averages(w, lin)
+    U = np.tile(avg[w.zext][:, None], (1, 8))
+    co = w.reconstruct(U)
+    pts = w.geo0["xg"][:, ::7]
+    val = w.evaluate(co, U, pts)[..., 3]
+    ok = interior(m, w.g)
+    assert np.abs(val - lin(pts))[ok].max() < 1e-12
+
+
+def test_central_fit_reproduces_polynomials(case):
+    """The central least-squares stage reproduces every polynomial of degree <= p-1
+    on the curved mapped zones (zone averages by exact cubature)."""
+    m, w = case
+    p = m.p
+    ex = taylor_exponents(p - 1, 0)
+    co = np.random.default_rng(5).standard_normal(len(ex))
+
+    def f(x):
+        v = np.zeros(x.shape[:-1])
+        for e, c in zip(ex, co):
+            v += c * x[..., 0] ** e[0] * x[..., 1] ** e[1] * x[..., 2] ** e[2]
+        return v
+
+    avg = averages(w, f)
+    U = avg[w.zext][:, None]
+    uH = np.einsum("zcj,zj->zc", w.pinv_central, avg[w.cidx] - U)
+    pts = w.geo0["xg"][:, ::5]
+    val = w.evaluate(uH[:, None, :], U, pts)[..., 0]
+    assert np.abs(val - f(pts)).max() < 1e-12 * max(1.0, np.abs(f(pts)).max())
+
+
+def test_smoothness_indicator_analytic():
+    """beta of P = a.s + c s_x^2 equals |a|^2 + 4 c^2 <s_x^2> + 4 a_x c <s_x> + (2c)^2 ...
+    computed here by direct cubature of the derivatives of a known polynomial."""
+    m = M.Mesh(3, 3, 1.0, 2.0, 3)
+    w = W.WenoAO(m)
+    rng = np.random.default_rng(6)
+    u = rng.standard_normal(w.nc1)
+    # direct: derivatives of P in scaled coordinates at cubature points of zone 0
+    g0 = w.geo0
+    s = (g0["xg"] - g0["xc"][:, None]) / g0["l0"][:, None, None]
+    ex = w.exps
+    grad = np.zeros(s.shape)
+    hess = np.zeros(s.shape[:2] + (6,))
+    for j, e in enumerate(ex):
+        for a in range(3):
+            if e[a] >= 1:
+                ee = e.copy()
+                ee[a] -= 1
+                grad[..., a] += u[j] * e[a] * np.prod(s ** ee, axis=-1)
+    # second derivatives are constants for p = 3: xx, xy, xz, yy, yz, zz
+    H = {(0, 0): 2 * u[3], (0, 1): u[4], (0, 2): u[5], (1, 1): 2 * u[6], (1, 2): u[7], (2, 2): 2 * u[8]}
+    direct = (np.einsum("zp,zp->z", g0["dV"], (grad ** 2).sum(-1)) / g0["V"]
+              + sum(v ** 2 for v in H.values()))
+    beta = np.einsum("c,zcd,d->z", u, w.Q, u)
+    assert np.abs(beta - direct).max() < 1e-12 * direct.max()
+
+
+def test_octant_stencils_are_face_neighbours():
+    m = M.Mesh(3, 3, 1.0, 2.0, 2)
+    st = W.Stencils(m)
+    for z in range(m.Z):
+        c, k = divmod(z, m.nr)
+        nbs = {st.face_nb(c, k, lf) for lf in range(6)}
+        assert set(map(tuple, st.central[z])) == nbs
+        for o in range(8):
+            assert set(map(tuple, st.octants[z][o])) <= nbs
