@@ -1,0 +1,304 @@
+"""Throughput of the full ADER-WENO-CT step on one GB300 (zone-updates/s).
+
+Workload (default): cubed-sphere mesh 6 x 32 x 32 angular zones x 32 log shells
+in r in [1, 2] (196,608 zones), 3rd order, FP64, smooth test problem
+(rho = 1 + 0.1 sin(2 pi (x+y+z)/sqrt3), p = 1, v = (.5,.5,.5), B = curl of
+A = 0.1 (sin 2 pi z, sin 2 pi x, sin 2 pi y)), dt from CFL 0.4 of the initial state.
+
+Timed region: K steps, each bracketed by CUDA events on the mesh stream, with an
+L2 flush (a 512 MB device write) between steps outside the events.  `value` is
+zone-updates/s with the state resident in HBM; `e2e` is the same metric through
+the C ABI with host (pinned) buffers: upload, step, download every step.
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on a
+bounded sample of the same workload and prints the same JSON line.
+Multi-GPU: the path is not sharded in this version ("replicas only"): each rank
+runs an independent replica; value = sum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s per full ADER-WENO-CT step (FP64 vs FP32-bulk), % roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--nr", type=int, default=32)
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-n", type=int, default=4)
+    ap.add_argument("--sample-nr", type=int, default=4)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return "cubed-sphere %dx%dx%d x %d shells (%d zones), order %d, FP64, smooth test" % (
+        6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+from oracle.step import Oracle
+from paper_1905_02504_gb300.inputs import make_problem
+o = Oracle(%(n)d, %(nr)d, 1.0, 2.0, %(p)d)
+U, phi = o.initial_state(make_problem("smooth"))
+dt = o.cfl_dt(U, %(cfl)r)
+times = []
+for s in range(%(steps)d):
+    t0 = time.perf_counter()
+    U, phi = o.step(U, phi, dt)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({"Z": o.mesh.Z, "times": times}))
+"""
+
+
+def run_oracle(n, nr, p, cfl, steps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET % dict(root=ROOT, n=n, nr=nr, p=p, cfl=cfl, steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3000)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(a):
+    res = run_oracle(a.sample_n, a.sample_nr, a.order, a.cfl, 1)
+    t = sum(res["times"])
+    return {"value": res["Z"] / t, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "1 FP64 oracle step of the same order-%d smooth test on the 6x%dx%dx%d mesh "
+                      "(%d zones), single thread, mesh setup excluded" % (
+                          a.order, a.sample_n, a.sample_n, a.sample_nr, res["Z"])}
+
+
+def reference_arm(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    res = run_oracle(a.sample_n, a.sample_nr, a.order, a.cfl, a.warmup + a.steps)
+    times = res["times"][a.warmup:]
+    Z = res["Z"]
+    total = sum(times)
+    value = Z * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "zone-updates/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "sample_zones": Z},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: one FP64 oracle step of the order-%d smooth test on "
+                                   "the 6x%dx%dx%d mesh (%d zones), single thread" % (
+                                       a.order, a.sample_n, a.sample_n, a.sample_nr, Z)},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def gpu_arm(a):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1905_02504_gb300 import geomhd
+    from paper_1905_02504_gb300.inputs import make_problem
+
+    stream = torch.cuda.Stream()
+    sid = stream.cuda_stream
+    mesh = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, stream=sid)
+    U0, phi0 = mesh.initial_state(make_problem("smooth"))
+    mesh.upload(U0, phi0)
+    dt = mesh.cfl_dt(a.cfl)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            mesh.step(dt)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    geomhd.geo_set_stage_timing(mesh.h, 1)
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    with torch.cuda.stream(stream):
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            mesh.step(dt)
+            ev[i][1].record(stream)
+    barrier()
+    clocks = clk.stop()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    geomhd.geo_set_stage_timing(mesh.h, 0)
+    stage_ms, stage_cnt = geomhd.geo_get_stage_timing(mesh.h)
+    t_ms = sum(step_ms)
+    if ws > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = tt.item()
+    Z = mesh.Z
+    value = ws * Z * a.steps / (t_ms * 1e-3)
+    a_div, r_div = mesh.divB()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    Uh = torch.from_numpy(U0).pin_memory()
+    ph = torch.from_numpy(phi0).pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    po = torch.empty_like(ph).pin_memory()
+    e2e_steps = max(3, min(a.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        geomhd.geo_state_upload(mesh.h, Uh, ph)
+        mesh.step(dt)
+        geomhd.geo_state_download(mesh.h, Uo, po)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    e2e_value = ws * Z * e2e_steps / t_e2e
+    bytes_state = (Uh.numel() + ph.numel()) * 8
+
+    # ---- roofline of the dominant kernel (plain FP64 ALU work)
+    flops, units = geomhd.geo_stage_flops(mesh.h)
+    avg = stage_ms / np.maximum(stage_cnt, 1)
+    top = int(np.argmax(avg))
+    achieved = flops[top] * units[top] / (avg[top] * 1e-3) / 1e12
+    fma_peak = geomhd.geo_probe_fma_peak(0, sid) / 1e12
+    nominal_fp64 = 1.25
+    roofline = {"bound": "alu", "achieved": achieved, "peak": nominal_fp64, "unit": "TFLOP/s",
+                "frac": achieved / nominal_fp64, "traffic": None, "kernel": "k_" + geomhd.STAGES[top],
+                "peak_kind": "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak,
+                "measured_fp64_fma_tflops": fma_peak}
+    stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
+              for s in range(geomhd.N_STAGES)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "zones": Z, "order": a.order, "dt": dt,
+                       "cfl": a.cfl, "l2": "flushed between steps (512 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "gpu_launches": int(geomhd.N_STAGES * a.steps),
+            "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": bytes_state,
+                    "d2h_bytes_per_step": bytes_state},
+            "roofline": roofline,
+            "stages": stages,
+            "divB_rel": r_div,
+            "clocks": clocks,
+        }
+        if not a.no_cpu_baseline:
+            try:
+                line["cpu_baseline"] = cpu_baseline(a)
+            except Exception as ex:  # reported, never fatal
+                line["cpu_baseline"] = {"error": str(ex)[:300]}
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+    else:
+        gpu_arm(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,158 @@
+/*
+ * geomhd.h -- C ABI of the GB300 implementation of the one-step ADER-WENO
+ * constrained-transport MHD scheme on a radially extruded cubed-sphere mesh of
+ * isoparametric hexahedra (Balsara, Florinski, Garain, Subramanian & Gurski,
+ * "Efficient, Divergence-Free, High Order MHD on 3D Spherical Meshes with Optimal
+ * Geodesic Meshing", arXiv 1905.02504).
+ *
+ * Conventions for every call
+ *   - Return value: GEO_OK (0) or a negative geo_status.  No call throws, aborts
+ *     or exits; geo_last_error() returns a message for the last failure of the
+ *     calling thread.
+ *   - The library owns all device memory of a mesh.  Buffers passed in are owned
+ *     by the caller and are never freed or retained by the library.
+ *   - Work runs on the CUDA stream given at creation (0 = legacy default stream).
+ *     Calls taking host pointers synchronise that stream before returning;
+ *     calls taking device pointers only enqueue work, except where noted.
+ *   - Units are rationalised (Heaviside-Lorentz): the Gaussian 1/(4 pi) of the
+ *     paper's Eq. 2.2 is absorbed into B (B_G = sqrt(4 pi) B).
+ *
+ * Numbering (identical in every call; n = subdiv, nr = radial shells)
+ *   columns        c = (f*n + j)*n + i  (cube face f in +x,+y,+z,-x,-y,-z order,
+ *                  equiangular indices i, j); ncol = 6 n^2
+ *   zones          z = c*nr + k,  k = 0 (innermost) .. nr-1;  Z = ncol*nr
+ *   sphere vertices / sphere edges: first appearance when scanning columns in
+ *                  order, corners (i,j),(i+1,j),(i,j+1),(i+1,j+1) and sides
+ *                  (j-side, i+1-side, j+1-side, i-side); an edge runs from its
+ *                  lower to its higher vertex id
+ *   faces          radial faces first: c*(nr+1) + k at radius r_k, normal +r;
+ *                  then angular faces F_rad + se*nr + k, normal along t x r
+ *   edges          radial edges first: sv*nr + k (r_k to r_k+1, direction +r);
+ *                  then angular edges E_rad + se*(nr+1) + k at r_k
+ *   r_k = r_in (r_out/r_in)^(k/nr)   (log-ratioed shells, paper Sec. V.b)
+ *
+ * State
+ *   U    : double[8][Z], structure of arrays, conserved zone averages
+ *          (rho, rho vx, rho vy, rho vz, energy, Bx, By, Bz); the zone B is the
+ *          helper field of paper Sec. IV (overwritten by the divergence-free
+ *          reconstruction at the start of every step).
+ *   phi  : double[F], magnetic flux through each face along its canonical
+ *          normal (the primal, Yee-staggered field of paper Sec. II.c).
+ */
+#ifndef GEOMHD_H
+#define GEOMHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct geo_mesh* geo_mesh_t;
+
+typedef enum {
+  GEO_OK = 0,
+  GEO_ERR_ARG = -1,          /* invalid argument (null pointer, bad size/order) */
+  GEO_ERR_OOM = -2,          /* device or host allocation failed               */
+  GEO_ERR_CUDA = -3,         /* a CUDA runtime call failed                       */
+  GEO_ERR_NONPHYSICAL = -4,  /* NaN/Inf or non-positive density/pressure seen    */
+  GEO_ERR_STATE = -6         /* call made before the state was uploaded          */
+} geo_status;
+
+typedef enum { GEO_FP64 = 0, GEO_FP32_BULK = 1 } geo_precision;
+
+/* Build the mesh and every geometric table on the host (FP64), then upload them.
+ * Mesh: paper Sec. II (geodesic mesh, radial extrusion, isoparametric mapping);
+ * tables: Eqs. 3.2-3.4 (Taylor moments, stencil least squares), Sec. IV.b steps
+ * 1-7 (KKT of the divergence-free reconstruction), Sec. V.d steps 1-4 (ADER
+ * matrices and nodal metrics).  Zones of one radial column are self-similar on
+ * log-ratioed shells, so tables are stored once per column (paper Sec. IV.b
+ * step 7, Sec. V.b).
+ *   subdiv  angular zones per cube-face edge (>= 2)
+ *   nr      radial shells (>= 2; >= 3 for order 4)
+ *   r_in, r_out   shell radii, 0 < r_in < r_out
+ *   order   2, 3 or 4 (scheme order p; map degree p-1)
+ *   prec    GEO_FP64 only in this version (GEO_FP32_BULK -> GEO_ERR_ARG)
+ *   stream  cudaStream_t cast to void* (0 = default stream)
+ *   out     receives the handle (NULL on failure)                              */
+int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order,
+                    int prec, void* stream, geo_mesh_t* out);
+int geo_mesh_destroy(geo_mesh_t mesh);
+
+/* Sizes of the zone, face and edge arrays (any pointer may be NULL). */
+int geo_mesh_sizes(geo_mesh_t mesh, int64_t* n_zones, int64_t* n_faces, int64_t* n_edges);
+
+/* Ratio gamma of specific heats (default 5/3). */
+int geo_set_gamma(geo_mesh_t mesh, double gamma);
+
+/* Zone cubature for initial data (host buffers, caller-owned):
+ * pts double[Z][nq^3][3] physical points, w double[Z][nq^3] physical weights
+ * (Jacobian included, summing to the zone volume); nq in 1..12 points per
+ * reference direction (tensor Gauss-Legendre on the isoparametric map, Eq. 5.5). */
+int geo_zone_cubature(geo_mesh_t mesh, int nq, double* pts, double* w);
+
+/* Edge quadrature for line integrals of a vector potential (host buffers):
+ * pts double[E][nq][3], tw double[E][nq][3] = unit tangent * |dl| * weight along
+ * the edge's canonical direction; nq in 1..12 (Gauss-Legendre).  Used to set
+ * divergence-free face fluxes from an edge circulation (paper Sec. VIII). */
+int geo_edge_quadrature(geo_mesh_t mesh, int nq, double* pts, double* tw);
+
+/* phi[f] = sum over the face's edges of sign * circ[e] (discrete Stokes;
+ * host buffers circ double[E], phi double[F]).  The result is exactly
+ * divergence-free per zone up to rounding. */
+int geo_phi_from_edge_circulation(geo_mesh_t mesh, const double* circ, double* phi);
+
+/* Zone centroids double[Z][3] and volumes double[Z] (host buffers). */
+int geo_zone_geometry(geo_mesh_t mesh, double* centroid, double* volume);
+
+/* Upload / download the state.  on_device != 0: U and phi are device pointers
+ * (stream-ordered copies); otherwise host pointers (the call synchronises). */
+int geo_state_upload(geo_mesh_t mesh, const double* U, const double* phi, int on_device);
+int geo_state_download(geo_mesh_t mesh, double* U, double* phi, int on_device);
+
+/* CFL time step, paper Sec. VII.b: dt = cfl * min_z d_z / (|v_z| + c_f,max,z) with
+ * the in-sphere diameter d_z = 6 V_z / S_z.  Device reduction; one scalar is read
+ * back (synchronises the stream). */
+int geo_cfl_dt(geo_mesh_t mesh, double cfl, double* dt);
+
+/* One full step of length dt (paper Sec. VI): WENO-AO reconstruction (Sec. III),
+ * divergence-free B reconstruction (Sec. IV), ADER-CG predictor (Sec. V), HLL
+ * face fluxes and multidimensional edge EMFs, finite-volume update of U and the
+ * Yee constrained-transport update of phi (Eqs. 2.5-2.6).  Asynchronous on the
+ * mesh stream. */
+int geo_step(geo_mesh_t mesh, double dt);
+
+/* Discrete divergence of the face fluxes (paper Sec. II.c): per zone
+ * sum_f s_zf phi_f; returns max |.| and max |.| / sum_f |phi_f| (synchronises). */
+int geo_divB_max(geo_mesh_t mesh, double* abs_max, double* rel_max);
+
+/* Per-stage device timing, accumulated with CUDA events on the mesh stream while
+ * enabled.  ms and counts: arrays of GEO_N_STAGES entries in the order
+ * weno, bperp, ader, face_flux, edge_emf, update_u, update_phi (host buffers). */
+#define GEO_N_STAGES 7
+int geo_set_stage_timing(geo_mesh_t mesh, int enable);
+int geo_get_stage_timing(geo_mesh_t mesh, double* ms, int64_t* counts);
+
+/* Algorithmic FP64 floating-point operations per zone of one geo_step stage,
+ * counted from the loop bounds of the method (order-dependent, host only). */
+int geo_stage_flops(geo_mesh_t mesh, double* flops_per_unit, int64_t* units);
+
+/* Measured FMA throughput of this GPU for the precision: a dependent-chain
+ * microbenchmark; result in floating-point operations per second (synchronises). */
+int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s);
+
+/* Copy one internal work buffer of the last step to host memory, for stage-by-
+ * stage verification: which = 0 WENO-AO Taylor coefficients [8][NC1][Z],
+ * 1 nodal normal B per face [NQmax][F], 2 predictor states at face points
+ * [M-1][NQT][8][Z], 3 predictor states at edge points [M-1][12][NS][8][Z],
+ * 4 time-integrated face fluxes [8][F], 5 time-integrated edge EMFs [E].
+ * count = number of doubles the host buffer holds; GEO_ERR_ARG if too small.
+ * Synchronises the stream. */
+int geo_debug_buffer(geo_mesh_t mesh, int which, double* host, int64_t count);
+
+const char* geo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEOMHD_H */

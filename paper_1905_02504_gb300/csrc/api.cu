@@ -1,0 +1,397 @@
+// C ABI (include/geomhd.h) of the GB300 ADER-WENO-CT MHD library.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/geomhd.h"
+#include "device.cuh"
+#include "host_tables.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return GEO_ERR_CUDA;
+}
+
+struct PendingTiming {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct geo_mesh {
+  geo::Tables T;
+  geo::DevTables dt{};
+  geo::DevState ds{};
+  cudaStream_t st = nullptr;
+  int order = 0;
+  bool have_state = false;
+  std::vector<void*> allocs;
+  bool timing = false;
+  std::vector<PendingTiming> pending;
+  double ms[geo::N_STAGES] = {};
+  int64_t cnt[geo::N_STAGES] = {};
+
+  template <typename Tv>
+  const Tv* upload(const std::vector<Tv>& v, cudaError_t& err) {
+    if (err != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    size_t bytes = v.size() * sizeof(Tv);
+    if (bytes == 0) bytes = sizeof(Tv);
+    err = cudaMalloc(&p, bytes);
+    if (err != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    if (!v.empty()) err = cudaMemcpy(p, v.data(), v.size() * sizeof(Tv), cudaMemcpyHostToDevice);
+    return static_cast<const Tv*>(p);
+  }
+  double* alloc(size_t n, cudaError_t& err) {
+    if (err != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    err = cudaMalloc(&p, (n ? n : 1) * sizeof(double));
+    if (err != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return static_cast<double*>(p);
+  }
+  void release() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    for (auto& t : pending) {
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+    pending.clear();
+  }
+};
+
+static int run_stage(geo_mesh* m, int stage, double dt) {
+  cudaError_t e = cudaSuccess;
+  PendingTiming pt{stage, nullptr, nullptr};
+  if (m->timing) {
+    cudaEventCreate(&pt.a);
+    cudaEventCreate(&pt.b);
+    cudaEventRecord(pt.a, m->st);
+  }
+  switch (m->order) {
+    case 2: e = geo::launch_stage<2>(stage, m->dt, m->ds, dt, m->st); break;
+    case 3: e = geo::launch_stage<3>(stage, m->dt, m->ds, dt, m->st); break;
+    default: e = geo::launch_stage<4>(stage, m->dt, m->ds, dt, m->st); break;
+  }
+  if (m->timing) {
+    cudaEventRecord(pt.b, m->st);
+    m->pending.push_back(pt);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GEO_OK;
+}
+
+extern "C" {
+
+const char* geo_last_error(void) { return g_err.c_str(); }
+
+int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, int prec, void* stream,
+                    geo_mesh_t* out) {
+  if (!out) return fail(GEO_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (prec != GEO_FP64) return fail(GEO_ERR_ARG, "only GEO_FP64 is available in this version");
+  auto* m = new (std::nothrow) geo_mesh();
+  if (!m) return fail(GEO_ERR_OOM, "host allocation failed");
+  std::string msg = geo::build_tables(subdiv, nr, r_in, r_out, order, m->T);
+  if (!msg.empty()) {
+    delete m;
+    return fail(GEO_ERR_ARG, msg);
+  }
+  m->order = order;
+  m->st = static_cast<cudaStream_t>(stream);
+  const geo::Tables& T = m->T;
+  const geo::Dims& d = T.d;
+  cudaError_t err = cudaSuccess;
+  geo::DevTables& D = m->dt;
+  D.n = T.n;
+  D.nr = T.nr;
+  D.ncol = T.ncol;
+  D.nsv = T.nsv;
+  D.nse = T.nse;
+  D.Z = T.Z;
+  D.F = T.F;
+  D.E = T.E;
+  D.F_rad = T.F_rad;
+  D.E_rad = T.E_rad;
+  D.gamma = 5.0 / 3.0;
+  std::vector<double> qpow(T.nr + 2);
+  for (int k = 0; k < T.nr + 2; ++k) qpow[k] = std::pow(T.q, k);
+  D.qpow = m->upload(qpow, err);
+  D.D = m->upload(T.D, err);
+  D.R = m->upload(T.R, err);
+  D.wt = m->upload(T.wt, err);
+  D.psiF = m->upload(T.psiF, err);
+  D.psiE = m->upload(T.psiE, err);
+  D.wE = m->upload(T.wE, err);
+  D.st_n = m->upload(T.st_n, err);
+  D.st_nb = m->upload(T.st_nb, err);
+  D.pinvH = m->upload(T.pinvH, err);
+  D.oct_nb = m->upload(T.oct_nb, err);
+  D.oct_inv = m->upload(T.oct_inv, err);
+  D.Q = m->upload(T.Q, err);
+  D.V0 = m->upload(T.V0, err);
+  D.l0 = m->upload(T.l0, err);
+  D.S0 = m->upload(T.S0, err);
+  D.A0 = m->upload(T.A0, err);
+  D.TF = m->upload(T.TF, err);
+  D.nF = m->upload(T.nF, err);
+  D.wF = m->upload(T.wF, err);
+  D.WF = m->upload(T.WF, err);
+  D.GB = m->upload(T.GB, err);
+  D.TN = m->upload(T.TN, err);
+  D.J0 = m->upload(T.J0, err);
+  D.Sm = m->upload(T.Sm, err);
+  D.gcl = m->upload(T.gcl, err);
+  D.JF = m->upload(T.JF, err);
+  D.JE = m->upload(T.JE, err);
+  D.col_side_se = m->upload(T.col_side_se, err);
+  D.col_side_sgn = m->upload(T.col_side_sgn, err);
+  D.se_v = m->upload(T.se_v, err);
+  D.se_col = m->upload(T.se_col, err);
+  D.se_lf = m->upload(T.se_lf, err);
+  D.se_perm = m->upload(T.se_perm, err);
+  D.se_le = m->upload(T.se_le, err);
+  D.se_rev = m->upload(T.se_rev, err);
+  D.se_t = m->upload(T.se_t, err);
+  D.se_dlw = m->upload(T.se_dlw, err);
+  D.se_nang = m->upload(T.se_nang, err);
+  D.se_nradL = m->upload(T.se_nradL, err);
+  D.se_nradR = m->upload(T.se_nradR, err);
+  D.sv_nc = m->upload(T.sv_nc, err);
+  D.sv_col = m->upload(T.sv_col, err);
+  D.sv_le = m->upload(T.sv_le, err);
+  D.sv_fL = m->upload(T.sv_fL, err);
+  D.sv_fR = m->upload(T.sv_fR, err);
+  D.sv_fn = m->upload(T.sv_fn, err);
+  D.sv_t = m->upload(T.sv_t, err);
+  D.sv_dlw = m->upload(T.sv_dlw, err);
+  const size_t Z = T.Z, F = T.F, E = T.E;
+  const int nqmax = d.NQR > d.NQS ? d.NQR : d.NQS;
+  geo::DevState& S = m->ds;
+  S.U = m->alloc(8 * Z, err);
+  S.phi = m->alloc(F, err);
+  S.Wc = m->alloc(static_cast<size_t>(8) * d.NC1 * Z, err);
+  S.Bp = m->alloc(static_cast<size_t>(nqmax) * F, err);
+  S.trF = m->alloc(static_cast<size_t>(d.M - 1) * d.NQT * 8 * Z, err);
+  S.trE = m->alloc(static_cast<size_t>(d.M - 1) * 12 * d.NS * 8 * Z, err);
+  S.Ff = m->alloc(8 * F, err);
+  S.Ee = m->alloc(E, err);
+  S.red = m->alloc(4096, err);
+  if (err != cudaSuccess) {
+    int code = (err == cudaErrorMemoryAllocation) ? GEO_ERR_OOM : GEO_ERR_CUDA;
+    std::string s = std::string("device setup: ") + cudaGetErrorString(err);
+    m->release();
+    delete m;
+    cudaGetLastError();
+    return fail(code, s);
+  }
+  *out = m;
+  return GEO_OK;
+}
+
+int geo_mesh_destroy(geo_mesh_t m) {
+  if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
+  cudaStreamSynchronize(m->st);
+  m->release();
+  delete m;
+  return GEO_OK;
+}
+
+int geo_mesh_sizes(geo_mesh_t m, int64_t* nz, int64_t* nf, int64_t* ne) {
+  if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
+  if (nz) *nz = m->T.Z;
+  if (nf) *nf = m->T.F;
+  if (ne) *ne = m->T.E;
+  return GEO_OK;
+}
+
+int geo_set_gamma(geo_mesh_t m, double gamma) {
+  if (!m || !(gamma > 1.0)) return fail(GEO_ERR_ARG, "need a mesh and gamma > 1");
+  m->dt.gamma = gamma;
+  return GEO_OK;
+}
+
+int geo_zone_cubature(geo_mesh_t m, int nq, double* pts, double* w) {
+  if (!m || !pts || !w || nq < 1 || nq > 12) return fail(GEO_ERR_ARG, "bad cubature arguments");
+  geo::zone_cubature(m->T, nq, pts, w);
+  return GEO_OK;
+}
+
+int geo_edge_quadrature(geo_mesh_t m, int nq, double* pts, double* tw) {
+  if (!m || !pts || !tw || nq < 1 || nq > 12) return fail(GEO_ERR_ARG, "bad quadrature arguments");
+  geo::edge_quadrature(m->T, nq, pts, tw);
+  return GEO_OK;
+}
+
+int geo_phi_from_edge_circulation(geo_mesh_t m, const double* circ, double* phi) {
+  if (!m || !circ || !phi) return fail(GEO_ERR_ARG, "bad arguments");
+  geo::phi_from_circulation(m->T, circ, phi);
+  return GEO_OK;
+}
+
+int geo_zone_geometry(geo_mesh_t m, double* xc, double* vol) {
+  if (!m || !xc || !vol) return fail(GEO_ERR_ARG, "bad arguments");
+  geo::zone_centroids(m->T, xc, vol);
+  return GEO_OK;
+}
+
+int geo_state_upload(geo_mesh_t m, const double* U, const double* phi, int on_device) {
+  if (!m || !U || !phi) return fail(GEO_ERR_ARG, "bad arguments");
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(m->ds.U, U, 8 * m->T.Z * sizeof(double), kind, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->ds.phi, phi, m->T.F * sizeof(double), kind, m->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "state upload");
+  m->have_state = true;
+  return GEO_OK;
+}
+
+int geo_state_download(geo_mesh_t m, double* U, double* phi, int on_device) {
+  if (!m || !U || !phi) return fail(GEO_ERR_ARG, "bad arguments");
+  if (!m->have_state) return fail(GEO_ERR_STATE, "no state uploaded");
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaMemcpyAsync(U, m->ds.U, 8 * m->T.Z * sizeof(double), kind, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phi, m->ds.phi, m->T.F * sizeof(double), kind, m->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "state download");
+  return GEO_OK;
+}
+
+int geo_cfl_dt(geo_mesh_t m, double cfl, double* dt) {
+  if (!m || !dt || !(cfl > 0.0)) return fail(GEO_ERR_ARG, "bad arguments");
+  if (!m->have_state) return fail(GEO_ERR_STATE, "no state uploaded");
+  cudaError_t e = geo::launch_cfl(m->dt, m->ds, cfl, dt, m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "cfl reduction");
+  if (!(*dt > 0.0) || !std::isfinite(*dt)) return fail(GEO_ERR_NONPHYSICAL, "non-physical state in CFL reduction");
+  return GEO_OK;
+}
+
+int geo_step(geo_mesh_t m, double dt) {
+  if (!m || !(dt > 0.0) || !std::isfinite(dt)) return fail(GEO_ERR_ARG, "bad arguments");
+  if (!m->have_state) return fail(GEO_ERR_STATE, "no state uploaded");
+  for (int s = 0; s < geo::N_STAGES; ++s) {
+    int rc = run_stage(m, s, dt);
+    if (rc != GEO_OK) return rc;
+  }
+  return GEO_OK;
+}
+
+int geo_divB_max(geo_mesh_t m, double* abs_max, double* rel_max) {
+  if (!m || !abs_max || !rel_max) return fail(GEO_ERR_ARG, "bad arguments");
+  if (!m->have_state) return fail(GEO_ERR_STATE, "no state uploaded");
+  double out[2] = {0, 0};
+  cudaError_t e = geo::launch_divb(m->dt, m->ds, out, m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "divB reduction");
+  *abs_max = out[0];
+  *rel_max = out[1];
+  return GEO_OK;
+}
+
+int geo_set_stage_timing(geo_mesh_t m, int enable) {
+  if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
+  m->timing = enable != 0;
+  return GEO_OK;
+}
+
+int geo_get_stage_timing(geo_mesh_t m, double* ms, int64_t* counts) {
+  if (!m || !ms || !counts) return fail(GEO_ERR_ARG, "bad arguments");
+  cudaError_t e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "timing sync");
+  for (auto& t : m->pending) {
+    float x = 0.f;
+    cudaEventElapsedTime(&x, t.a, t.b);
+    m->ms[t.stage] += x;
+    m->cnt[t.stage] += 1;
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  m->pending.clear();
+  for (int s = 0; s < geo::N_STAGES; ++s) {
+    ms[s] = m->ms[s];
+    counts[s] = m->cnt[s];
+    m->ms[s] = 0.0;
+    m->cnt[s] = 0;
+  }
+  return GEO_OK;
+}
+
+int geo_stage_flops(geo_mesh_t m, double* fl, int64_t* units) {
+  if (!m || !fl || !units) return fail(GEO_ERR_ARG, "bad arguments");
+  const geo::Dims& d = m->T.d;
+  const double N = d.N, M = d.M, NC1 = d.NC1, NQT = d.NQT, NS = d.NS, P = d.P, NBIN = d.NBIN;
+  const double nq_mean = NQT / 6.0;
+  double ns = 0;
+  for (int v : m->T.st_n) ns += v;
+  ns /= m->T.ncol;
+  const double flux = 40.0;   // one physical flux F(U).n with its primitive recovery
+  const double hll = 2 * flux + 60.0;
+  // WENO-AO, per zone and variable: central LSQ apply, smoothness form, 8 octant fits
+  fl[geo::ST_WENO] = 8.0 * (ns * (1 + 2 * NC1) + 2 * NC1 * NC1 + 2 * NC1 + 8 * (3 + 18 + 6 + 4) + 3 * 48 + 2 * NC1);
+  units[geo::ST_WENO] = m->T.Z;
+  // nodal normal B per face: two polynomial evaluations per point, MinMod, shift
+  fl[geo::ST_BPERP] = nq_mean * (2 * (3 * 2 * NC1 + 5) + 8);
+  units[geo::ST_BPERP] = m->T.F;
+  // ADER: KKT apply + node values, p Picard sweeps over M-1 levels (+ level 1 once),
+  // each with N flux evaluations in 4 directions and the 3 N x N contractions
+  const double levels = 1 + P * (M - 1);
+  const double per_level = N * (4 * flux + 8) + 3 * 2 * N * N * 8;
+  fl[geo::ST_ADER] = 2 * (3 + 3 * N) * NBIN + N * 5 * 2 * NC1 + levels * per_level +
+                     P * (M - 1) * N * 8 * 2 * M + (M - 1) * (NQT + 12 * NS) * (N * 8 * 2 + 8);
+  units[geo::ST_ADER] = m->T.Z;
+  fl[geo::ST_FACE] = (M - 1) * nq_mean * (hll + 16);
+  units[geo::ST_FACE] = m->T.F;
+  fl[geo::ST_EDGE] = (M - 1) * NS * (4 * 16 + 4 * (2 * 45 + 20) + 4);
+  units[geo::ST_EDGE] = m->T.E;
+  fl[geo::ST_UPD_U] = 6 * 8 * 2 + 8;
+  units[geo::ST_UPD_U] = m->T.Z;
+  fl[geo::ST_UPD_PHI] = 4;
+  units[geo::ST_UPD_PHI] = m->T.F;
+  return GEO_OK;
+}
+
+int geo_debug_buffer(geo_mesh_t m, int which, double* host, int64_t count) {
+  if (!m || !host) return fail(GEO_ERR_ARG, "bad arguments");
+  const geo::Dims& d = m->T.d;
+  const int64_t Z = m->T.Z, F = m->T.F, E = m->T.E;
+  const int nqmax = d.NQR > d.NQS ? d.NQR : d.NQS;
+  const double* src = nullptr;
+  int64_t n = 0;
+  switch (which) {
+    case 0: src = m->ds.Wc; n = 8LL * d.NC1 * Z; break;
+    case 1: src = m->ds.Bp; n = static_cast<int64_t>(nqmax) * F; break;
+    case 2: src = m->ds.trF; n = static_cast<int64_t>(d.M - 1) * d.NQT * 8 * Z; break;
+    case 3: src = m->ds.trE; n = static_cast<int64_t>(d.M - 1) * 12 * d.NS * 8 * Z; break;
+    case 4: src = m->ds.Ff; n = 8 * F; break;
+    case 5: src = m->ds.Ee; n = E; break;
+    default: return fail(GEO_ERR_ARG, "unknown buffer");
+  }
+  if (count < n) return fail(GEO_ERR_ARG, "host buffer too small");
+  cudaError_t e = cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "debug copy");
+  return GEO_OK;
+}
+
+int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s) {
+  if (!flops_per_s) return fail(GEO_ERR_ARG, "bad arguments");
+  cudaError_t e = geo::probe_fma(prec, static_cast<cudaStream_t>(stream), flops_per_s);
+  if (e != cudaSuccess) return cuda_fail(e, "fma probe");
+  return GEO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Device-side declarations shared by the kernels and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace geo {
+
+template <int P> struct Dim;
+template <> struct Dim<2> {
+  static constexpr int N = 8, M = 2, NC1 = 3, NC = 4, NB = 7, NQR = 4, NQS = 4, NQT = 24, NS = 1,
+                       SMAX = 6, NBIN = 3 * NC + NQT + 6;
+};
+template <> struct Dim<3> {
+  static constexpr int N = 20, M = 3, NC1 = 9, NC = 10, NB = 16, NQR = 4, NQS = 4, NQT = 24, NS = 2,
+                       SMAX = 26, NBIN = 3 * NC + NQT + 6;
+};
+template <> struct Dim<4> {
+  static constexpr int N = 32, M = 4, NC1 = 19, NC = 20, NB = 30, NQR = 9, NQS = 6, NQT = 42, NS = 3,
+                       SMAX = 32, NBIN = 3 * NC + NQT + 6;
+};
+
+// Read-only tables in device memory (see host_tables.h for the layouts).
+struct DevTables {
+  int n, nr, ncol, nsv, nse;
+  long long Z, F, E, F_rad, E_rad;
+  double gamma;
+  const double* qpow;  // [nr + 2]: q^k
+  const double *D, *R, *wt, *psiF, *psiE, *wE;
+  const int* st_n;
+  const int* st_nb;
+  const double* pinvH;
+  const int* oct_nb;
+  const double *oct_inv, *Q, *V0, *l0, *S0, *A0, *TF, *nF, *wF, *WF, *GB, *TN, *J0, *Sm, *gcl, *JF, *JE;
+  const int *col_side_se, *col_side_sgn;
+  const int *se_v, *se_col, *se_lf, *se_perm, *se_le, *se_rev;
+  const double *se_t, *se_dlw, *se_nang, *se_nradL, *se_nradR;
+  const int *sv_nc, *sv_col, *sv_le, *sv_fL, *sv_fR;
+  const double *sv_fn, *sv_t, *sv_dlw;
+};
+
+// Mutable device state and work arrays of one mesh.
+struct DevState {
+  double* U;     // [8][Z]
+  double* phi;   // [F]
+  double* Wc;    // [8*NC1][Z] WENO-AO Taylor coefficients
+  double* Bp;    // [NQmax][F]  nodal normal B per face (canonical orientation)
+  double* trF;   // [(M-1)*NQT*8][Z] predictor states at the zone's face points
+  double* trE;   // [(M-1)*12*NS*8][Z] predictor states at the zone's edge points
+  double* Ff;    // [8][F] time-integrated face fluxes
+  double* Ee;    // [E]   time-integrated edge EMFs
+  double* red;   // reduction scratch
+};
+
+enum Stage { ST_WENO = 0, ST_BPERP, ST_ADER, ST_FACE, ST_EDGE, ST_UPD_U, ST_UPD_PHI, N_STAGES };
+
+// launchers (kernels.cu); return cudaGetLastError() of the launch
+template <int P>
+cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, double dt, cudaStream_t st);
+cudaError_t launch_cfl(const DevTables& T, const DevState& S, double cfl, double* out_host,
+                       cudaStream_t st);
+cudaError_t launch_divb(const DevTables& T, const DevState& S, double* out2_host, cudaStream_t st);
+cudaError_t probe_fma(int prec, cudaStream_t st, double* flops_per_s);
+int reduction_blocks(long long n);
+
+}  // namespace geo

@@ -1,0 +1,123 @@
+"""GPU path vs the FP64 oracle, stage by stage and over several full steps.
+
+Both sides start from the same seeded state (the oracle's zone averages and
+edge-circulation face fluxes); the GPU runs through the C ABI.  Tolerance: the
+per-variable relative L1 of 1e-12 required for the FP64 form, on meshes that
+span several thread blocks and end in a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from conftest import gpu_available
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+def rel_l1(a, b, axis=None):
+    num = np.abs(a - b).sum(axis=axis)
+    den = np.abs(b).sum(axis=axis)
+    return num / np.maximum(den, 1e-300)
+
+
+_CACHE = {}
+
+
+def setup_case(n, nr, p, problem="smooth"):
+    from oracle.step import Oracle
+    from paper_1905_02504_gb300 import geomhd
+    from paper_1905_02504_gb300.inputs import make_problem
+    key = (n, nr, p)
+    if key not in _CACHE:
+        _CACHE[key] = Oracle(n, nr, 1.0, 2.0, p)
+    o = _CACHE[key]
+    pr = make_problem(problem) if problem != "uniform" else make_problem("uniform", B0=(0.3, -0.2, 0.5))
+    U, phi = o.initial_state(pr)
+    m = geomhd.Mesh(n, nr, 1.0, 2.0, p)
+    assert (m.Z, m.F, m.E) == (o.mesh.Z, o.mesh.F, o.mesh.E)
+    m.upload(np.ascontiguousarray(U.T), phi.copy())
+    return o, m, U, phi
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not gpu_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("n,nr,p", [(5, 3, 2), (4, 4, 3)])
+def test_stages_match_oracle(n, nr, p):
+    from paper_1905_02504_gb300 import geomhd
+    o, m, U, phi = setup_case(n, nr, p)
+    dt = o.cfl_dt(U, 0.4)
+    dt_gpu = m.cfl_dt(0.4)
+    assert abs(dt_gpu - dt) <= 1e-13 * dt
+    U1, phi1, st = o.step(U, phi, dt, return_stages=True)
+    m.step(dt)
+    Ug, phig = m.download()
+    om = o.mesh
+    Z, F, E = om.Z, om.F, om.E
+    nc1 = o.weno.nc1
+    # a1: WENO-AO coefficients
+    W = geomhd.geo_debug_buffer(m.h, 0, 8 * nc1 * Z).reshape(8, nc1, Z)
+    Wo = np.transpose(st["coeffs"], (1, 2, 0))
+    for v in range(8):
+        assert rel_l1(W[v], Wo[v]) < RTOL, ("weno", v, rel_l1(W[v], Wo[v]))
+    # a2: nodal normal fields per face
+    nqmax = max(o.dfb.nq)
+    Bp = geomhd.geo_debug_buffer(m.h, 1, nqmax * F).reshape(nqmax, F)
+    Bo = np.zeros((nqmax, F))
+    mask = np.zeros((nqmax, F), bool)
+    for f, b in st["bperp"].items():
+        Bo[:len(b), f] = b
+        mask[:len(b), f] = True
+    assert rel_l1(Bp[mask], Bo[mask]) < RTOL
+    # a3: predictor states at face points
+    M = p
+    nqt = sum(o.dfb.nq)
+    trF = geomhd.geo_debug_buffer(m.h, 2, (M - 1) * nqt * 8 * Z).reshape(M - 1, nqt, 8, Z)
+    tro = np.concatenate([o.ader.point_values(st["Uh"], o.face_ref[lf]) for lf in range(6)], axis=2)
+    tro = np.transpose(tro[:, 1:], (1, 2, 3, 0))
+    for v in range(8):
+        assert rel_l1(trF[:, :, v], tro[:, :, v]) < RTOL, ("traces", v)
+    # a4, a5: face fluxes and edge EMFs
+    Ff = geomhd.geo_debug_buffer(m.h, 4, 8 * F).reshape(8, F)
+    for v in range(8):
+        assert rel_l1(Ff[v], st["Fface"][:, v]) < RTOL, ("face flux", v, rel_l1(Ff[v], st["Fface"][:, v]))
+    Ee = geomhd.geo_debug_buffer(m.h, 5, E)
+    assert rel_l1(Ee, st["Eedge"]) < RTOL
+    # a6: updated state
+    for v in range(8):
+        assert rel_l1(Ug[v], U1[:, v]) < RTOL, ("U", v, rel_l1(Ug[v], U1[:, v]))
+    assert rel_l1(phig, phi1) < RTOL
+    m.close()
+
+
+@pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 10), (4, 4, 3, 4)])
+def test_multistep_parity_and_divb(n, nr, p, steps):
+    o, m, U, phi = setup_case(n, nr, p)
+    dt = o.cfl_dt(U, 0.4)
+    for _ in range(steps):
+        U, phi = o.step(U, phi, dt)
+        m.step(dt)
+    Ug, phig = m.download()
+    for v in range(8):
+        assert rel_l1(Ug[v], U[:, v]) < RTOL, (v, rel_l1(Ug[v], U[:, v]))
+    assert rel_l1(phig, phi) < RTOL
+    a, r = m.divB()
+    assert r < 1e-13
+    m.close()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_free_stream_on_gpu(p):
+    o, m, U, phi = setup_case(4, 3, p, problem="uniform")
+    dt = m.cfl_dt(0.3)
+    for _ in range(3):
+        m.step(dt)
+    Ug, phig = m.download()
+    dev = np.abs(Ug - U.T).max(axis=1) / np.abs(U).max(axis=0)
+    assert dev.max() < 1e-13, dev
+    assert np.abs(phig - phi).max() < 1e-13 * np.abs(phi).max()
+    m.close()
