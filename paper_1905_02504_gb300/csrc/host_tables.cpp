@@ -898,6 +898,9 @@ struct Builder {
         for (int s = 0; s < NS; ++s) {
           auto h = map_jac(X, edge_point(le, te[s]));
           T.sv_dlw[static_cast<size_t>(v) * NS + s] = norm(h[2]) * we[s];
+          // radial edge: x = rho(zeta) P_v, so the tangent is the vertex direction
+          if (s == 0)
+            for (int a = 0; a < 3; ++a) T.sv_t[3 * v + a] = h[2][a] / norm(h[2]);
         }
       }
       int nf = static_cast<int>(sv_edges[v].size());
