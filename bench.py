@@ -177,6 +177,20 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
+def captured_traffic(a, kernel, Z):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu capture,
+    scaled by zones; None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1905_02504_gb300", "csrc", "kernels.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["kernels_cu_sha256_prefix"] or rec["order"] != a.order:
+            return None
+        return rec["dram_bytes_per_zone"] * Z
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -259,7 +273,8 @@ def gpu_arm(a):
     fma_peak = geomhd.geo_probe_fma_peak(0, sid) / 1e12
     nominal_fp64 = 1.25
     roofline = {"bound": "alu", "achieved": achieved, "peak": nominal_fp64, "unit": "TFLOP/s",
-                "frac": achieved / nominal_fp64, "traffic": None, "kernel": "k_" + geomhd.STAGES[top],
+                "frac": achieved / nominal_fp64, "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], Z),
+                "kernel": "k_" + geomhd.STAGES[top],
                 "peak_kind": "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak,
                 "measured_fp64_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
