@@ -150,6 +150,25 @@ int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s);
  * Synchronises the stream. */
 int geo_debug_buffer(geo_mesh_t mesh, int which, double* host, int64_t count);
 
+/* CFL time step for callers that cannot allocate device memory at the time of
+ * the call (a memory pool owned by another component, a rule against device
+ * synchronisation, externally managed buffers).  No counterpart in the paper:
+ * the same quantity as geo_cfl_dt, computed without any allocation.
+ *   U_dev  device double[8][Z], caller-owned conserved variables (same layout as
+ *          geo_state_upload); read only
+ *   dt_dev device double[1], caller-owned; receives cfl * min_z d_z/(|v|+c_f),
+ *          or a non-positive value when a state is non-physical
+ * The call only enqueues two kernels on the mesh stream (no synchronisation, no
+ * cudaMalloc/cudaFree or any allocating routine).  Scratch: a fixed device
+ * array of GEO_NOALLOC_MAX_BLOCKS doubles (512 KB per GPU, kept until exit), so
+ * meshes of more than GEO_NOALLOC_MAX_BLOCKS * 256 zones are rejected with
+ * GEO_ERR_ARG.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Calls share the array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller. */
+#define GEO_NOALLOC_MAX_BLOCKS 65536
+int geo_cfl_dt_noalloc(geo_mesh_t mesh, const double* U_dev, double cfl, double* dt_dev);
+
 const char* geo_last_error(void);
 
 #ifdef __cplusplus

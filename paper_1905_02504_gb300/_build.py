@@ -1,6 +1,6 @@
 """In-tree build of the CUDA library libgeomhd.so for sm_103a (nvcc, no cmake).
 
-The three translation units compile in parallel, then link into
+The translation units compile in parallel, then link into
 paper_1905_02504_gb300/lib/libgeomhd.so.  Rebuilds only when a source is newer
 than the library.
 """
@@ -16,7 +16,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgeomhd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host_tables.cpp", "kernels.cu", "api.cu"]
+SOURCES = ["host_tables.cpp", "kernels.cu", "api.cu", "noalloc.cu"]
 
 
 def _nvcc():

@@ -96,6 +96,13 @@ static int run_stage(geo_mesh* m, int stage, double dt) {
   return GEO_OK;
 }
 
+namespace geo {
+// accessors used by the allocation-free entry point (noalloc.cu)
+const DevTables* mesh_dev_tables(const geo_mesh* m) { return &m->dt; }
+cudaStream_t mesh_stream(const geo_mesh* m) { return m->st; }
+void set_error_message(const std::string& msg) { g_err = msg; }
+}  // namespace geo
+
 extern "C" {
 
 const char* geo_last_error(void) { return g_err.c_str(); }

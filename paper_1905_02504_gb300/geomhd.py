@@ -50,6 +50,7 @@ _SIGS = {
     "geo_stage_flops": [_h, _vp, _vp],
     "geo_probe_fma_peak": [ctypes.c_int, _vp, _pd],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
+    "geo_cfl_dt_noalloc": [_h, _vp, _d, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -194,6 +195,13 @@ def geo_debug_buffer(h, which, count):
     out = np.empty(count)
     _check(_lib.geo_debug_buffer(h, which, _ptr(out), count), "geo_debug_buffer")
     return out
+
+
+def geo_cfl_dt_noalloc(h, U_dev, cfl, dt_dev):
+    """Allocation-free CFL step: U_dev (8, Z) and dt_dev (1,) are caller-owned CUDA
+    float64 tensors; only enqueues work on the mesh stream."""
+    assert _is_device(U_dev) and _is_device(dt_dev)
+    _check(_lib.geo_cfl_dt_noalloc(h, _ptr(U_dev), cfl, _ptr(dt_dev)), "geo_cfl_dt_noalloc")
 
 
 def geo_last_error():
