@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
+    ap.add_argument("--compare-steps", type=int, default=10)
     ap.add_argument("--sample-n", type=int, default=4)
     ap.add_argument("--sample-nr", type=int, default=4)
     return ap.parse_args()
@@ -191,6 +193,68 @@ def captured_traffic(a, kernel, Z):
         return None
 
 
+def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
+    """The FP32-bulk form on the same workload: throughput over the same timed
+    protocol, roofline of its dominant kernel against the FP32 ALU peak, and its
+    per-variable relative L1 error against the FP64 form after the same steps
+    from the same initial state (the FP64 form matches the oracle to 1e-12)."""
+    import numpy as np
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    sid = stream.cuda_stream
+    m32 = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, prec=geomhd.GEO_FP32_BULK, stream=sid)
+    m32.upload(U0, phi0)
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            m32.step(dt)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    geomhd.geo_set_stage_timing(m32.h, 1)
+    barrier()
+    with torch.cuda.stream(stream):
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            m32.step(dt)
+            ev[i][1].record(stream)
+    barrier()
+    t_ms = sum(s.elapsed_time(e) for s, e in ev)
+    geomhd.geo_set_stage_timing(m32.h, 0)
+    stage_ms, stage_cnt = geomhd.geo_get_stage_timing(m32.h)
+    avg = stage_ms / np.maximum(stage_cnt, 1)
+    top = int(np.argmax(avg))
+    flops, units = geomhd.geo_stage_flops(m32.h)
+    achieved = flops[top] * units[top] / (avg[top] * 1e-3) / 1e12
+    fp32_probe = geomhd.geo_probe_fma_peak(1, sid) / 1e12
+    nominal_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    # error against the FP64 form after the same number of steps
+    mesh64.upload(U0, phi0)
+    m32.upload(U0, phi0)
+    for _ in range(a.compare_steps):
+        mesh64.step(dt)
+        m32.step(dt)
+    U64, p64 = mesh64.download()
+    U32, p32 = m32.download()
+    err = [float(np.abs(U32[v] - U64[v]).sum() / np.abs(U64[v]).sum()) for v in range(8)]
+    errp = float(np.abs(p32 - p64).sum() / np.abs(p64).sum())
+    _, r32 = m32.divB()
+    out = {
+        "value": ws * m32.Z * a.steps / (t_ms * 1e-3), "unit": "zone-updates/s",
+        "ms_per_step": t_ms / a.steps, "dtype": "f32 bulk / f64 accumulation and updates",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / nominal_fp32, "traffic": None, "kernel": "k_" + geomhd.STAGES[top],
+                     "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
+                                  "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
+                     "measured_fp32_fma_tflops": fp32_probe},
+        "stages": {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
+                   for s in range(geomhd.N_STAGES)},
+        "rel_l1_vs_fp64": err, "rel_l1_phi_vs_fp64": errp, "steps_compared": a.compare_steps,
+        "divB_rel": r32,
+    }
+    m32.close()
+    return out
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -279,6 +343,7 @@ def gpu_arm(a):
                 "measured_fp64_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
+    fp32 = None if a.no_fp32 else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
@@ -296,6 +361,8 @@ def gpu_arm(a):
             "divB_rel": r_div,
             "clocks": clocks,
         }
+        if fp32 is not None:
+            line["fp32_bulk"] = fp32
         if not a.no_cpu_baseline:
             try:
                 line["cpu_baseline"] = cpu_baseline(a)

@@ -72,7 +72,11 @@ typedef enum { GEO_FP64 = 0, GEO_FP32_BULK = 1 } geo_precision;
  *   nr      radial shells (>= 2; >= 3 for order 4)
  *   r_in, r_out   shell radii, 0 < r_in < r_out
  *   order   2, 3 or 4 (scheme order p; map degree p-1)
- *   prec    GEO_FP64 only in this version (GEO_FP32_BULK -> GEO_ERR_ARG)
+ *   prec    GEO_FP64: every step in FP64.  GEO_FP32_BULK: reconstruction, the
+ *           divergence-free fit, the predictor and the Riemann solvers in FP32
+ *           (FP32 copies of the per-column matrices, FP64 masters kept on the
+ *           device); face-flux and edge-EMF integrals accumulated in FP64 and
+ *           the updates of U and phi in FP64, so div B stays at FP64 rounding
  *   stream  cudaStream_t cast to void* (0 = default stream)
  *   out     receives the handle (NULL on failure)                              */
 int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order,
@@ -144,7 +148,8 @@ int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s);
 /* Copy one internal work buffer of the last step to host memory, for stage-by-
  * stage verification: which = 0 WENO-AO Taylor coefficients [8][NC1][Z],
  * 1 nodal normal B per face [NQmax][F], 2 predictor states at face points
- * [M-1][NQT][8][Z], 3 predictor states at edge points [M-1][12][NS][8][Z],
+ * [M-1][NQT][8][Z], 3 predictor states at edge points [M-1][12][NS][8][Z]
+ * (buffers 0-3 are FP32 in the FP32-bulk form and are widened to double),
  * 4 time-integrated face fluxes [8][F], 5 time-integrated edge EMFs [E].
  * count = number of doubles the host buffer holds; GEO_ERR_ARG if too small.
  * Synchronises the stream. */

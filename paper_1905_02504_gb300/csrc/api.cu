@@ -37,6 +37,7 @@ struct geo_mesh {
   geo::DevState ds{};
   cudaStream_t st = nullptr;
   int order = 0;
+  int prec = GEO_FP64;
   bool have_state = false;
   std::vector<void*> allocs;
   bool timing = false;
@@ -55,6 +56,20 @@ struct geo_mesh {
     allocs.push_back(p);
     if (!v.empty()) err = cudaMemcpy(p, v.data(), v.size() * sizeof(Tv), cudaMemcpyHostToDevice);
     return static_cast<const Tv*>(p);
+  }
+  // FP32 copy of an FP64 table (made once; the FP64 master stays on the device)
+  const float* upload_f32(const std::vector<double>& v, cudaError_t& err) {
+    std::vector<float> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) f[i] = static_cast<float>(v[i]);
+    return upload(f, err);
+  }
+  void* alloc_bytes(size_t n, cudaError_t& err) {
+    if (err != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    err = cudaMalloc(&p, n ? n : 1);
+    if (err != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return p;
   }
   double* alloc(size_t n, cudaError_t& err) {
     if (err != cudaSuccess) return nullptr;
@@ -83,10 +98,14 @@ static int run_stage(geo_mesh* m, int stage, double dt) {
     cudaEventCreate(&pt.b);
     cudaEventRecord(pt.a, m->st);
   }
+  const bool f32 = m->prec == GEO_FP32_BULK;
   switch (m->order) {
-    case 2: e = geo::launch_stage<2>(stage, m->dt, m->ds, dt, m->st); break;
-    case 3: e = geo::launch_stage<3>(stage, m->dt, m->ds, dt, m->st); break;
-    default: e = geo::launch_stage<4>(stage, m->dt, m->ds, dt, m->st); break;
+    case 2: e = f32 ? geo::launch_stage<2, float>(stage, m->dt, m->ds, dt, m->st)
+                    : geo::launch_stage<2, double>(stage, m->dt, m->ds, dt, m->st); break;
+    case 3: e = f32 ? geo::launch_stage<3, float>(stage, m->dt, m->ds, dt, m->st)
+                    : geo::launch_stage<3, double>(stage, m->dt, m->ds, dt, m->st); break;
+    default: e = f32 ? geo::launch_stage<4, float>(stage, m->dt, m->ds, dt, m->st)
+                     : geo::launch_stage<4, double>(stage, m->dt, m->ds, dt, m->st); break;
   }
   if (m->timing) {
     cudaEventRecord(pt.b, m->st);
@@ -111,7 +130,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
                     geo_mesh_t* out) {
   if (!out) return fail(GEO_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (prec != GEO_FP64) return fail(GEO_ERR_ARG, "only GEO_FP64 is available in this version");
+  if (prec != GEO_FP64 && prec != GEO_FP32_BULK) return fail(GEO_ERR_ARG, "prec must be GEO_FP64 or GEO_FP32_BULK");
   auto* m = new (std::nothrow) geo_mesh();
   if (!m) return fail(GEO_ERR_OOM, "host allocation failed");
   std::string msg = geo::build_tables(subdiv, nr, r_in, r_out, order, m->T);
@@ -120,6 +139,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
     return fail(GEO_ERR_ARG, msg);
   }
   m->order = order;
+  m->prec = prec;
   m->st = static_cast<cudaStream_t>(stream);
   const geo::Tables& T = m->T;
   const geo::Dims& d = T.d;
@@ -162,6 +182,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.GB = m->upload(T.GB, err);
   D.TN = m->upload(T.TN, err);
   D.J0 = m->upload(T.J0, err);
+  D.iJ0 = m->upload(T.iJ0, err);
   D.Sm = m->upload(T.Sm, err);
   D.gcl = m->upload(T.gcl, err);
   D.JF = m->upload(T.JF, err);
@@ -187,15 +208,42 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.sv_fn = m->upload(T.sv_fn, err);
   D.sv_t = m->upload(T.sv_t, err);
   D.sv_dlw = m->upload(T.sv_dlw, err);
+  // bulk-arithmetic views of the per-column matrices
+  D.b64 = geo::BulkTables<double>{D.pinvH, D.oct_inv, D.Q, D.TF, D.nF, D.wF, D.GB, D.TN, D.J0, D.iJ0,
+                                  D.Sm, D.gcl, D.JF, D.JE};
+  const bool f32 = prec == GEO_FP32_BULK;
+  if (f32) {
+    geo::BulkTables<float>& b = D.b32;
+    b.pinvH = m->upload_f32(T.pinvH, err);
+    b.oct_inv = m->upload_f32(T.oct_inv, err);
+    b.Q = m->upload_f32(T.Q, err);
+    b.TF = m->upload_f32(T.TF, err);
+    b.nF = m->upload_f32(T.nF, err);
+    b.wF = m->upload_f32(T.wF, err);
+    b.GB = m->upload_f32(T.GB, err);
+    b.TN = m->upload_f32(T.TN, err);
+    b.J0 = m->upload_f32(T.J0, err);
+    b.iJ0 = m->upload_f32(T.iJ0, err);
+    b.Sm = m->upload_f32(T.Sm, err);
+    b.gcl = m->upload_f32(T.gcl, err);
+    b.JF = m->upload_f32(T.JF, err);
+    b.JE = m->upload_f32(T.JE, err);
+  }
+  if (err == cudaSuccess) {
+    if (order == 2) err = f32 ? geo::upload_reference_constants<2, float>(T) : geo::upload_reference_constants<2, double>(T);
+    else if (order == 3) err = f32 ? geo::upload_reference_constants<3, float>(T) : geo::upload_reference_constants<3, double>(T);
+    else err = f32 ? geo::upload_reference_constants<4, float>(T) : geo::upload_reference_constants<4, double>(T);
+  }
   const size_t Z = T.Z, F = T.F, E = T.E;
   const int nqmax = d.NQR > d.NQS ? d.NQR : d.NQS;
   geo::DevState& S = m->ds;
   S.U = m->alloc(8 * Z, err);
   S.phi = m->alloc(F, err);
-  S.Wc = m->alloc(static_cast<size_t>(8) * d.NC1 * Z, err);
-  S.Bp = m->alloc(static_cast<size_t>(nqmax) * F, err);
-  S.trF = m->alloc(static_cast<size_t>(d.M - 1) * d.NQT * 8 * Z, err);
-  S.trE = m->alloc(static_cast<size_t>(d.M - 1) * 12 * d.NS * 8 * Z, err);
+  const size_t rb = f32 ? sizeof(float) : sizeof(double);
+  S.Wc = m->alloc_bytes(rb * 8 * d.NC1 * Z, err);
+  S.Bp = m->alloc_bytes(rb * nqmax * F, err);
+  S.trF = m->alloc_bytes(rb * (d.M - 1) * d.NQT * 8 * Z, err);
+  S.trE = m->alloc_bytes(rb * (d.M - 1) * 12 * d.NS * 8 * Z, err);
   S.Ff = m->alloc(8 * F, err);
   S.Ee = m->alloc(E, err);
   S.red = m->alloc(4096, err);
@@ -345,20 +393,25 @@ int geo_stage_flops(geo_mesh_t m, double* fl, int64_t* units) {
   double ns = 0;
   for (int v : m->T.st_n) ns += v;
   ns /= m->T.ncol;
-  const double flux = 40.0;   // one physical flux F(U).n with its primitive recovery
-  const double hll = 2 * flux + 60.0;
+  const double flux1 = 40.0;  // one physical flux F(U).n with its primitive recovery
+  const double hll = 2 * flux1 + 60.0;
   // WENO-AO, per zone and variable: central LSQ apply, smoothness form, 8 octant fits
   fl[geo::ST_WENO] = 8.0 * (ns * (1 + 2 * NC1) + 2 * NC1 * NC1 + 2 * NC1 + 8 * (3 + 18 + 6 + 4) + 3 * 48 + 2 * NC1);
   units[geo::ST_WENO] = m->T.Z;
   // nodal normal B per face: two polynomial evaluations per point, MinMod, shift
   fl[geo::ST_BPERP] = nq_mean * (2 * (3 * 2 * NC1 + 5) + 8);
   units[geo::ST_BPERP] = m->T.F;
-  // ADER: KKT apply + node values, p Picard sweeps over M-1 levels (+ level 1 once),
-  // each with N flux evaluations in 4 directions and the 3 N x N contractions
+  // ADER: KKT apply + node values, then 1 + p (M-1) flux-difference levels, each
+  // with N primitive recoveries, 4 physical fluxes per node (3 metric directions
+  // + the geometric-conservation residual) and the 3 NNZ nonzero couplings of the
+  // serendipity derivative matrices over 8 variables; p Picard updates of M-1
+  // levels; point values at the face (edge) points from the face's (edge's) nodes
   const double levels = 1 + P * (M - 1);
-  const double per_level = N * (4 * flux + 8) + 3 * 2 * N * N * 8;
+  const double flux = 45.0, prim = 17.0;
+  const double per_level = N * (8 + prim + 4 * flux + 8) + 3.0 * d.NNZ * 8 * 2;
   fl[geo::ST_ADER] = 2 * (3 + 3 * N) * NBIN + N * 5 * 2 * NC1 + levels * per_level +
-                     P * (M - 1) * N * 8 * 2 * M + (M - 1) * (NQT + 12 * NS) * (N * 8 * 2 + 8);
+                     P * (M - 1) * N * 8 * 2 * M +
+                     (M - 1) * (NQT * (d.NFN * 16 + 8) + 12 * NS * (d.NEN * 16 + 8));
   units[geo::ST_ADER] = m->T.Z;
   fl[geo::ST_FACE] = (M - 1) * nq_mean * (hll + 16);
   units[geo::ST_FACE] = m->T.F;
@@ -376,20 +429,29 @@ int geo_debug_buffer(geo_mesh_t m, int which, double* host, int64_t count) {
   const geo::Dims& d = m->T.d;
   const int64_t Z = m->T.Z, F = m->T.F, E = m->T.E;
   const int nqmax = d.NQR > d.NQS ? d.NQR : d.NQS;
-  const double* src = nullptr;
+  const void* src = nullptr;
   int64_t n = 0;
+  bool bulk = true;
   switch (which) {
     case 0: src = m->ds.Wc; n = 8LL * d.NC1 * Z; break;
     case 1: src = m->ds.Bp; n = static_cast<int64_t>(nqmax) * F; break;
     case 2: src = m->ds.trF; n = static_cast<int64_t>(d.M - 1) * d.NQT * 8 * Z; break;
     case 3: src = m->ds.trE; n = static_cast<int64_t>(d.M - 1) * 12 * d.NS * 8 * Z; break;
-    case 4: src = m->ds.Ff; n = 8 * F; break;
-    case 5: src = m->ds.Ee; n = E; break;
+    case 4: src = m->ds.Ff; n = 8 * F; bulk = false; break;
+    case 5: src = m->ds.Ee; n = E; bulk = false; break;
     default: return fail(GEO_ERR_ARG, "unknown buffer");
   }
   if (count < n) return fail(GEO_ERR_ARG, "host buffer too small");
-  cudaError_t e = cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, m->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  cudaError_t e;
+  if (bulk && m->prec == GEO_FP32_BULK) {
+    std::vector<float> tmp(n);
+    e = cudaMemcpyAsync(tmp.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    for (int64_t i = 0; i < n; ++i) host[i] = tmp[i];
+  } else {
+    e = cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "debug copy");
   return GEO_OK;
 }

@@ -8,15 +8,36 @@ namespace geo {
 template <int P> struct Dim;
 template <> struct Dim<2> {
   static constexpr int N = 8, M = 2, NC1 = 3, NC = 4, NB = 7, NQR = 4, NQS = 4, NQT = 24, NS = 1,
-                       SMAX = 6, NBIN = 3 * NC + NQT + 6;
+                       SMAX = 6, NBIN = 3 * NC + NQT + 6, NNZ = 16, NFN = 4, NEN = 2;
 };
 template <> struct Dim<3> {
   static constexpr int N = 20, M = 3, NC1 = 9, NC = 10, NB = 16, NQR = 4, NQS = 4, NQT = 24, NS = 2,
-                       SMAX = 26, NBIN = 3 * NC + NQT + 6;
+                       SMAX = 26, NBIN = 3 * NC + NQT + 6, NNZ = 96, NFN = 8, NEN = 3;
 };
 template <> struct Dim<4> {
   static constexpr int N = 32, M = 4, NC1 = 19, NC = 20, NB = 30, NQR = 9, NQS = 6, NQT = 42, NS = 3,
-                       SMAX = 32, NBIN = 3 * NC + NQT + 6;
+                       SMAX = 32, NBIN = 3 * NC + NQT + 6, NNZ = 192, NFN = 12, NEN = 4;
+};
+
+// Reference-element constants of one order in the bulk arithmetic type R, kept
+// in constant memory (every thread of a warp reads the same entry, so the
+// constant cache broadcasts).
+template <int P, typename R> struct RefConst {
+  R Dval[3 * Dim<P>::NNZ];                      // CSC values of D^xi, D^eta, D^zeta
+  unsigned char Drow[3 * Dim<P>::NNZ];          // row (node i) of each value
+  unsigned short Dptr[3 * (Dim<P>::N + 1)];     // column (node j) pointers
+  R psiFc[Dim<P>::NQT * Dim<P>::NFN];           // face-node basis at the face points
+  unsigned char fnode[6 * Dim<P>::NFN];
+  R psiEc[12 * Dim<P>::NS * Dim<P>::NEN];       // edge-node basis at the edge points
+  unsigned char enode[12 * Dim<P>::NEN];
+  R R_[Dim<P>::M * Dim<P>::M];
+};
+
+// Per-column matrices used by the bulk arithmetic, in its type R.  The FP64
+// form points at the FP64 tables; the FP32-bulk form at FP32 copies made once
+// at mesh creation (the FP64 masters stay on the device).
+template <typename R> struct BulkTables {
+  const R *pinvH, *oct_inv, *Q, *TF, *nF, *wF, *GB, *TN, *J0, *iJ0, *Sm, *gcl, *JF, *JE;
 };
 
 // Read-only tables in device memory (see host_tables.h for the layouts).
@@ -30,31 +51,39 @@ struct DevTables {
   const int* st_nb;
   const double* pinvH;
   const int* oct_nb;
-  const double *oct_inv, *Q, *V0, *l0, *S0, *A0, *TF, *nF, *wF, *WF, *GB, *TN, *J0, *Sm, *gcl, *JF, *JE;
+  const double *oct_inv, *Q, *V0, *l0, *S0, *A0, *TF, *nF, *wF, *WF, *GB, *TN, *J0, *iJ0, *Sm, *gcl, *JF, *JE;
   const int *col_side_se, *col_side_sgn;
   const int *se_v, *se_col, *se_lf, *se_perm, *se_le, *se_rev;
   const double *se_t, *se_dlw, *se_nang, *se_nradL, *se_nradR;
   const int *sv_nc, *sv_col, *sv_le, *sv_fL, *sv_fR;
   const double *sv_fn, *sv_t, *sv_dlw;
+  BulkTables<double> b64;
+  BulkTables<float> b32;
 };
 
 // Mutable device state and work arrays of one mesh.
+// Work arrays marked (R) hold the bulk arithmetic type (double or float).
 struct DevState {
   double* U;     // [8][Z]
   double* phi;   // [F]
-  double* Wc;    // [8*NC1][Z] WENO-AO Taylor coefficients
-  double* Bp;    // [NQmax][F]  nodal normal B per face (canonical orientation)
-  double* trF;   // [(M-1)*NQT*8][Z] predictor states at the zone's face points
-  double* trE;   // [(M-1)*12*NS*8][Z] predictor states at the zone's edge points
-  double* Ff;    // [8][F] time-integrated face fluxes
-  double* Ee;    // [E]   time-integrated edge EMFs
+  void* Wc;      // (R) [8*NC1][Z] WENO-AO Taylor coefficients
+  void* Bp;      // (R) [NQmax][F]  nodal normal B per face (canonical orientation)
+  void* trF;     // (R) [(M-1)*NQT*8][Z] predictor states at the zone's face points
+  void* trE;     // (R) [(M-1)*12*NS*8][Z] predictor states at the zone's edge points
+  double* Ff;    // [8][F] time-integrated face fluxes (FP64 accumulation)
+  double* Ee;    // [E]   time-integrated edge EMFs (FP64 accumulation)
   double* red;   // reduction scratch
 };
 
 enum Stage { ST_WENO = 0, ST_BPERP, ST_ADER, ST_FACE, ST_EDGE, ST_UPD_U, ST_UPD_PHI, N_STAGES };
 
+struct Tables;
+// copy the order-P reference constants into constant memory in type R (kernels.cu)
+template <int P, typename R>
+cudaError_t upload_reference_constants(const Tables& T);
+
 // launchers (kernels.cu); return cudaGetLastError() of the launch
-template <int P>
+template <int P, typename R>
 cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, double dt, cudaStream_t st);
 cudaError_t launch_cfl(const DevTables& T, const DevState& S, double cfl, double* out_host,
                        cudaStream_t st);

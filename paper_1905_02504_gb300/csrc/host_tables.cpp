@@ -189,6 +189,9 @@ Dims dims_for_order(int p) {
   d.G = (p == 4) ? 2 : 1;
   d.NDIV = d.NC1;
   d.NBIN = 3 * d.NC + d.NQT + 6;
+  d.NNZ = (p == 2) ? 16 : (p == 3 ? 96 : 192);
+  d.NFN = (p == 2) ? 4 : (p == 3 ? 8 : 12);
+  d.NEN = p;
   return d;
 }
 
@@ -660,6 +663,7 @@ struct Builder {
       Sn[i][1] = cross(h[2], h[0]);
       Sn[i][2] = cross(h[0], h[1]);
       T.J0[static_cast<size_t>(c) * N + i] = J[i];
+      T.iJ0[static_cast<size_t>(c) * N + i] = 1.0 / J[i];
       for (int al = 0; al < 3; ++al)
         for (int b = 0; b < 3; ++b) T.Sm[((static_cast<size_t>(c) * 3 + al) * N + i) * 3 + b] = Sn[i][al][b];
       V3 s;
@@ -930,6 +934,89 @@ struct Builder {
     }
   }
 
+  // CSC lists of D^alpha and the face / edge supports of the point evaluations
+  std::string sparse_forms() {
+    const int N = d.N, NS = d.NS, NQT = d.NQT;
+    double dmax = 0.0;
+    for (double v : T.D) dmax = std::max(dmax, std::fabs(v));
+    const double tol = 1e-13 * dmax;
+    T.Dptr.assign(3 * (N + 1), 0);
+    T.Drow.clear();
+    T.Dval.clear();
+    for (int a = 0; a < 3; ++a) {
+      int cnt = 0;
+      for (int j = 0; j < N; ++j) {
+        T.Dptr[a * (N + 1) + j] = cnt;
+        for (int i = 0; i < N; ++i) {
+          double v = T.D[(static_cast<size_t>(a) * N + i) * N + j];
+          if (std::fabs(v) > tol) {
+            T.Drow.push_back(i);
+            T.Dval.push_back(v);
+            ++cnt;
+          }
+        }
+      }
+      T.Dptr[a * (N + 1) + N] = cnt;
+      if (cnt != d.NNZ) return "internal: unexpected sparsity of the derivative matrices";
+    }
+    T.fnode.assign(6 * d.NFN, 0);
+    T.psiFc.assign(static_cast<size_t>(NQT) * d.NFN, 0.0);
+    for (int lf = 0; lf < 6; ++lf) {
+      int cnt = 0;
+      for (int i = 0; i < N; ++i)
+        if (el.nodes[i][FACE_AXIS[lf]] == FACE_SIDE[lf]) {
+          if (cnt >= d.NFN) return "internal: face node count";
+          T.fnode[lf * d.NFN + cnt++] = i;
+        }
+      if (cnt != d.NFN) return "internal: face node count";
+      for (int q = T.foff[lf]; q < T.foff[lf + 1]; ++q)
+        for (int i = 0; i < N; ++i) {
+          double v = T.psiF[static_cast<size_t>(q) * N + i];
+          int a = -1;
+          for (int t = 0; t < d.NFN; ++t)
+            if (T.fnode[lf * d.NFN + t] == i) a = t;
+          if (a < 0) {
+            if (std::fabs(v) > 1e-12) return "internal: basis not supported on the face nodes";
+          } else {
+            T.psiFc[static_cast<size_t>(q) * d.NFN + a] = v;
+          }
+        }
+    }
+    T.enode.assign(12 * d.NEN, 0);
+    T.psiEc.assign(static_cast<size_t>(12) * NS * d.NEN, 0.0);
+    for (int le = 0; le < 12; ++le) {
+      int ax = EDGE_AXIS[le];
+      int cnt = 0;
+      for (int i = 0; i < N; ++i) {
+        bool on = true;
+        int qq = 0;
+        for (int a = 0; a < 3; ++a) {
+          if (a == ax) continue;
+          if (el.nodes[i][a] != EDGE_FIX[le][qq]) on = false;
+          ++qq;
+        }
+        if (on) {
+          if (cnt >= d.NEN) return "internal: edge node count";
+          T.enode[le * d.NEN + cnt++] = i;
+        }
+      }
+      if (cnt != d.NEN) return "internal: edge node count";
+      for (int s = 0; s < NS; ++s)
+        for (int i = 0; i < N; ++i) {
+          double v = T.psiE[(static_cast<size_t>(le) * NS + s) * N + i];
+          int a = -1;
+          for (int t = 0; t < d.NEN; ++t)
+            if (T.enode[le * d.NEN + t] == i) a = t;
+          if (a < 0) {
+            if (std::fabs(v) > 1e-12) return "internal: basis not supported on the edge nodes";
+          } else {
+            T.psiEc[(static_cast<size_t>(le) * NS + s) * d.NEN + a] = v;
+          }
+        }
+    }
+    return "";
+  }
+
   std::string build() {
     T.d = d;
     T.n = n;
@@ -1013,6 +1100,10 @@ struct Builder {
           el.basis(xi.data(), &T.psiE[(static_cast<size_t>(le) * NS + s) * N]);
         }
     }
+    {
+      std::string msg = sparse_forms();
+      if (!msg.empty()) return msg;
+    }
     topology();
     T.Z = static_cast<int64_t>(ncol) * nr;
     T.F_rad = static_cast<int64_t>(ncol) * (nr + 1);
@@ -1039,6 +1130,7 @@ struct Builder {
     T.GB.assign(nc * (3 + 3 * N) * d.NBIN, 0.0);
     T.TN.assign(nc * N * d.NC1, 0.0);
     T.J0.assign(nc * N, 0.0);
+    T.iJ0.assign(nc * N, 0.0);
     T.Sm.assign(nc * 9 * N, 0.0);
     T.gcl.assign(nc * N * 3, 0.0);
     T.JF.assign(nc * NQT, 0.0);

@@ -25,6 +25,9 @@ struct Dims {
   int G;     // ghost shells
   int NDIV;  // divergence constraints
   int NBIN;  // inputs of the divergence-free reconstruction
+  int NNZ;   // nonzeros of one derivative matrix D^alpha
+  int NFN;   // nodes on one face
+  int NEN;   // nodes on one edge
 };
 Dims dims_for_order(int p);
 
@@ -42,6 +45,15 @@ struct Tables {
   std::vector<double> psiE;  // [12][NS][N]
   std::vector<double> wE;    // [NS]
   std::vector<int> foff;     // [7]        offsets of the local faces in NQT
+  // sparse forms (the serendipity derivative matrices are sparse, and a basis
+  // function restricted to a face / edge only involves that face's / edge's nodes)
+  std::vector<int> Dptr;     // [3][N+1]   column pointers of D^alpha (CSC)
+  std::vector<int> Drow;     // [3][NNZ]
+  std::vector<double> Dval;  // [3][NNZ]
+  std::vector<int> fnode;    // [6][NFN]   nodes of each local face
+  std::vector<double> psiFc; // [NQT][NFN] basis of those nodes at the face points
+  std::vector<int> enode;    // [12][NEN]  nodes of each local edge
+  std::vector<double> psiEc; // [12*NS][NEN]
 
   // per column (zone at shell 0)
   std::vector<int> st_n;       // [ncol]
@@ -60,6 +72,7 @@ struct Tables {
   std::vector<double> GB;      // [ncol][3+3N][NBIN]
   std::vector<double> TN;      // [ncol][N][NC1]   Taylor basis at the nodes
   std::vector<double> J0;      // [ncol][N]
+  std::vector<double> iJ0;     // [ncol][N]        1 / J0
   std::vector<double> Sm;      // [ncol][3][N][3]  h_eta x h_zeta, h_zeta x h_xi, h_xi x h_eta
   std::vector<double> gcl;     // [ncol][N][3]
   std::vector<double> JF;      // [ncol][NQT]      interpolated J at face points

@@ -1,49 +1,82 @@
-// CUDA kernels of one ADER-WENO-CT step (arXiv 1905.02504, Sec. VI), FP64.
+// CUDA kernels of one ADER-WENO-CT step (arXiv 1905.02504, Sec. VI).
 //
 // One thread per zone / face / edge.  Zones of a radial column share their
 // tables (self-similar log shells, Sec. IV.b step 7 and Sec. V.b): zone (c, k)
 // reads column c's tables and rescales lengths by q^k, areas by q^2k and
 // volumes by q^3k.  Per-zone arrays are structure-of-arrays ([component][Z]) so
 // consecutive threads touch consecutive addresses.
+//
+// Precision: the reconstruction, the predictor and the Riemann solvers run in
+// the bulk type R (double for the FP64 form, float for the FP32-bulk form);
+// the time-integrated face fluxes and edge EMFs are accumulated in FP64 and the
+// updates of U and Phi are FP64 in both forms, so div B stays at FP64 rounding.
 #include "device.cuh"
+#include "host_tables.h"
 
 #include <cfloat>
 
 namespace geo {
 
+__constant__ RefConst<2, double> c_ref2d;
+__constant__ RefConst<3, double> c_ref3d;
+__constant__ RefConst<4, double> c_ref4d;
+__constant__ RefConst<2, float> c_ref2f;
+__constant__ RefConst<3, float> c_ref3f;
+__constant__ RefConst<4, float> c_ref4f;
+
+template <int P, typename R> struct RC;
+#define GEO_RC(P, R, SYM)                                                              \
+  template <> struct RC<P, R> {                                                         \
+    static __device__ __forceinline__ const RefConst<P, R>& get() { return SYM; }       \
+    static const RefConst<P, R>& sym() { return SYM; }                                  \
+  };
+GEO_RC(2, double, c_ref2d)
+GEO_RC(3, double, c_ref3d)
+GEO_RC(4, double, c_ref4d)
+GEO_RC(2, float, c_ref2f)
+GEO_RC(3, float, c_ref3f)
+GEO_RC(4, float, c_ref4f)
+#undef GEO_RC
+
 namespace {
 
 constexpr int TPB = 128;
 
+template <typename R> __device__ __forceinline__ const BulkTables<R>& bulk(const DevTables& T);
+template <> __device__ __forceinline__ const BulkTables<double>& bulk<double>(const DevTables& T) { return T.b64; }
+template <> __device__ __forceinline__ const BulkTables<float>& bulk<float>(const DevTables& T) { return T.b32; }
+
 // ----------------------------------------------------------------------------
-// ideal MHD (Eq. 2.2 in rationalised units)
+// ideal MHD (Eq. 2.2 in rationalised units), in the bulk type R
 // ----------------------------------------------------------------------------
+template <typename R>
 struct Prim {
-  double rho, vx, vy, vz, p, bx, by, bz;
+  R rho, vx, vy, vz, p, bx, by, bz;
 };
 
-__device__ __forceinline__ Prim to_prim(const double* u, double g) {
-  Prim w;
+template <typename R>
+__device__ __forceinline__ Prim<R> to_prim(const R* u, R g) {
+  Prim<R> w;
   w.rho = u[0];
-  double ir = 1.0 / u[0];
+  R ir = R(1) / u[0];
   w.vx = u[1] * ir;
   w.vy = u[2] * ir;
   w.vz = u[3] * ir;
   w.bx = u[5];
   w.by = u[6];
   w.bz = u[7];
-  w.p = (g - 1.0) * (u[4] - 0.5 * w.rho * (w.vx * w.vx + w.vy * w.vy + w.vz * w.vz) -
-                     0.5 * (w.bx * w.bx + w.by * w.by + w.bz * w.bz));
+  w.p = (g - R(1)) * (u[4] - R(0.5) * w.rho * (w.vx * w.vx + w.vy * w.vy + w.vz * w.vz) -
+                      R(0.5) * (w.bx * w.bx + w.by * w.by + w.bz * w.bz));
   return w;
 }
 
 // F(U).n for any vector n
-__device__ __forceinline__ void flux_n(const double* u, const Prim& w, double nx, double ny, double nz,
-                                       double* F) {
-  double vn = w.vx * nx + w.vy * ny + w.vz * nz;
-  double bn = w.bx * nx + w.by * ny + w.bz * nz;
-  double pt = w.p + 0.5 * (w.bx * w.bx + w.by * w.by + w.bz * w.bz);
-  double vb = w.vx * w.bx + w.vy * w.by + w.vz * w.bz;
+template <typename R>
+__device__ __forceinline__ void flux_n(const R* u, const Prim<R>& w, R nx, R ny, R nz, R* F) {
+  R vn = w.vx * nx + w.vy * ny + w.vz * nz;
+  R bn = w.bx * nx + w.by * ny + w.bz * nz;
+  R pt = w.p + R(0.5) * (w.bx * w.bx + w.by * w.by + w.bz * w.bz);
+  R vb = w.vx * w.bx + w.vy * w.by + w.vz * w.bz;
   F[0] = w.rho * vn;
   F[1] = u[1] * vn + pt * nx - w.bx * bn;
   F[2] = u[2] * vn + pt * ny - w.by * bn;
@@ -54,49 +87,55 @@ __device__ __forceinline__ void flux_n(const double* u, const Prim& w, double nx
   F[7] = w.bz * vn - w.vz * bn;
 }
 
-__device__ __forceinline__ double fast_speed(const Prim& w, double nx, double ny, double nz, double g) {
-  double ir = 1.0 / w.rho;
-  double a2 = g * w.p * ir;
-  double b2 = (w.bx * w.bx + w.by * w.by + w.bz * w.bz) * ir;
-  double bn = w.bx * nx + w.by * ny + w.bz * nz;
-  double bn2 = bn * bn * ir;
-  double s = a2 + b2;
-  return sqrt(0.5 * (s + sqrt(fmax(s * s - 4.0 * a2 * bn2, 0.0))));
+template <typename R>
+__device__ __forceinline__ R fast_speed(const Prim<R>& w, R nx, R ny, R nz, R g) {
+  R ir = R(1) / w.rho;
+  R a2 = g * w.p * ir;
+  R b2 = (w.bx * w.bx + w.by * w.by + w.bz * w.bz) * ir;
+  R bn = w.bx * nx + w.by * ny + w.bz * nz;
+  R bn2 = bn * bn * ir;
+  R s = a2 + b2;
+  return sqrt(R(0.5) * (s + sqrt(fmax(s * s - R(4) * a2 * bn2, R(0)))));
 }
 
-// HLL flux along the unit normal (Davis wave speeds), accumulated with weight w
-__device__ __forceinline__ void hll_acc(const double* uL, const double* uR, double nx, double ny, double nz,
-                                        double g, double w, double* acc) {
-  Prim a = to_prim(uL, g), b = to_prim(uR, g);
-  double vnL = a.vx * nx + a.vy * ny + a.vz * nz;
-  double vnR = b.vx * nx + b.vy * ny + b.vz * nz;
-  double cL = fast_speed(a, nx, ny, nz, g), cR = fast_speed(b, nx, ny, nz, g);
-  double SL = fmin(vnL - cL, vnR - cR);
-  double SR = fmax(vnL + cL, vnR + cR);
-  double FL[8], FR[8];
+// HLL flux along the unit normal (Davis wave speeds); the weighted flux is
+// accumulated in FP64
+template <typename R>
+__device__ __forceinline__ void hll_acc(const R* uL, const R* uR, R nx, R ny, R nz, R g, double w,
+                                        double* acc) {
+  Prim<R> a = to_prim(uL, g), b = to_prim(uR, g);
+  R vnL = a.vx * nx + a.vy * ny + a.vz * nz;
+  R vnR = b.vx * nx + b.vy * ny + b.vz * nz;
+  R cL = fast_speed(a, nx, ny, nz, g), cR = fast_speed(b, nx, ny, nz, g);
+  R SL = fmin(vnL - cL, vnR - cR);
+  R SR = fmax(vnL + cL, vnR + cR);
+  R FL[8], FR[8];
   flux_n(uL, a, nx, ny, nz, FL);
   flux_n(uR, b, nx, ny, nz, FR);
-  if (SL >= 0.0) {
+  if (SL >= R(0)) {
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * FL[v];
-  } else if (SR <= 0.0) {
+    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FL[v]);
+  } else if (SR <= R(0)) {
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * FR[v];
+    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FR[v]);
   } else {
-    double id = 1.0 / (SR - SL);
+    R id = R(1) / (SR - SL);
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * ((SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * id);
+    for (int v = 0; v < 8; ++v)
+      acc[v] += w * static_cast<double>((SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * id);
   }
 }
 
-__device__ __forceinline__ double rusanov_speed(const double* u, double nx, double ny, double nz, double g) {
-  Prim w = to_prim(u, g);
+template <typename R>
+__device__ __forceinline__ R rusanov_speed(const R* u, R nx, R ny, R nz, R g) {
+  Prim<R> w = to_prim(u, g);
   return fabs(w.vx * nx + w.vy * ny + w.vz * nz) + fast_speed(w, nx, ny, nz, g);
 }
 
-__device__ __forceinline__ double minmod(double a, double b) {
-  if (a * b > 0.0) return (a > 0.0 ? 1.0 : -1.0) * fmin(fabs(a), fabs(b));
-  return 0.0;
+template <typename R>
+__device__ __forceinline__ R minmod(R a, R b) {
+  if (a * b > R(0)) return (a > R(0) ? R(1) : R(-1)) * fmin(fabs(a), fabs(b));
+  return R(0);
 }
 
 __device__ __forceinline__ int side_of_lf(int lf) { return lf == 0 ? 3 : (lf == 1 ? 1 : (lf == 2 ? 0 : 2)); }
@@ -155,14 +194,15 @@ __device__ __forceinline__ FaceInfo face_info(const DevTables& T, long long f) {
 // ----------------------------------------------------------------------------
 // a1: WENO-AO reconstruction (Sec. III)
 // ----------------------------------------------------------------------------
-template <int P>
+template <int P, typename R>
 __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* __restrict__ U,
-                                              double* __restrict__ Wc) {
+                                              R* __restrict__ Wc) {
   using Dm = Dim<P>;
   constexpr int NC1 = Dm::NC1, SMAX = Dm::SMAX;
-  const double GH = 0.85, GK = 0.15 / 8.0, EPS = 1e-12;
+  const R GH = R(0.85), GK = R(0.15 / 8.0), EPS = R(1e-12);
   long long z = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (z >= T.Z) return;
+  const BulkTables<R>& B = bulk<R>(T);
   const long long Z = T.Z;
   int nr = T.nr;
   int c = static_cast<int>(z / nr), k = static_cast<int>(z % nr);
@@ -182,49 +222,51 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
     int kk = min(max(k + dk, 0), nr - 1);
     zo[j] = static_cast<long long>(cc) * nr + kk;
   }
-  const double* pinv = T.pinvH + static_cast<size_t>(c) * NC1 * SMAX;
-  const double* oinv = T.oct_inv + static_cast<size_t>(c) * 72;
-  const double* Qm = T.Q + static_cast<size_t>(c) * NC1 * NC1;
+  const R* pinv = B.pinvH + static_cast<size_t>(c) * NC1 * SMAX;
+  const R* oinv = B.oct_inv + static_cast<size_t>(c) * 72;
+  const R* Qm = B.Q + static_cast<size_t>(c) * NC1 * NC1;
 #pragma unroll 1
   for (int v = 0; v < 8; ++v) {
     const double* Uv = U + v * Z;
-    double u0 = Uv[z];
-    double uH[NC1];
+    const double u0d = Uv[z];
+    const R u0 = static_cast<R>(u0d);
+    R uH[NC1];
 #pragma unroll
-    for (int m = 0; m < NC1; ++m) uH[m] = 0.0;
+    for (int m = 0; m < NC1; ++m) uH[m] = R(0);
     for (int j = 0; j < ns; ++j) {
-      double du = Uv[zs[j]] - u0;
+      R du = static_cast<R>(Uv[zs[j]] - u0d);
 #pragma unroll
       for (int m = 0; m < NC1; ++m) uH[m] += pinv[m * SMAX + j] * du;
     }
-    double bH = 0.0;
+    R bH = R(0);
 #pragma unroll
     for (int i = 0; i < NC1; ++i) {
-      double s = 0.0;
+      R s = R(0);
 #pragma unroll
       for (int j = 0; j < NC1; ++j) s += Qm[i * NC1 + j] * uH[j];
       bH += uH[i] * s;
     }
-    double wH = GH / ((bH + EPS) * (bH + EPS));
-    double tot = wH;
-    double uK[8][3], wK[8];
+    R wH = GH / ((bH + EPS) * (bH + EPS));
+    R tot = wH;
+    R uK[8][3], wK[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      double d0 = Uv[zo[3 * o]] - u0, d1 = Uv[zo[3 * o + 1]] - u0, d2 = Uv[zo[3 * o + 2]] - u0;
-      const double* A = oinv + 9 * o;
+      R d0 = static_cast<R>(Uv[zo[3 * o]] - u0d), d1 = static_cast<R>(Uv[zo[3 * o + 1]] - u0d),
+        d2 = static_cast<R>(Uv[zo[3 * o + 2]] - u0d);
+      const R* A = oinv + 9 * o;
 #pragma unroll
       for (int a = 0; a < 3; ++a) uK[o][a] = A[3 * a] * d0 + A[3 * a + 1] * d1 + A[3 * a + 2] * d2;
-      double b = uK[o][0] * uK[o][0] + uK[o][1] * uK[o][1] + uK[o][2] * uK[o][2];
+      R b = uK[o][0] * uK[o][0] + uK[o][1] * uK[o][1] + uK[o][2] * uK[o][2];
       wK[o] = GK / ((b + EPS) * (b + EPS));
       tot += wK[o];
     }
-    double itot = 1.0 / tot;
+    R itot = R(1) / tot;
     wH *= itot;
-    double fH = wH / GH;
-    double* out = Wc + static_cast<size_t>(v) * NC1 * Z;
+    R fH = wH / GH;
+    R* out = Wc + static_cast<size_t>(v) * NC1 * Z;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double sk = 0.0, wk = 0.0;
+      R sk = R(0), wk = R(0);
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         sk += uK[o][a];
@@ -234,35 +276,38 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
     }
 #pragma unroll
     for (int m = 3; m < NC1; ++m) out[m * Z + z] = fH * uH[m];
+    (void)u0;
   }
 }
 
 // ----------------------------------------------------------------------------
 // a2 (face part): nodal normal fields by MinMod + mean shift (Eqs. 4.11-4.12)
 // ----------------------------------------------------------------------------
-template <int P>
+template <int P, typename R>
 __global__ void __launch_bounds__(TPB) k_bperp(const DevTables T, const double* __restrict__ U,
-                                               const double* __restrict__ phi, const double* __restrict__ Wc,
-                                               double* __restrict__ Bp) {
+                                               const double* __restrict__ phi, const R* __restrict__ Wc,
+                                               R* __restrict__ Bp) {
   using Dm = Dim<P>;
   constexpr int NC1 = Dm::NC1, NQT = Dm::NQT, NQMAX = (Dm::NQR > Dm::NQS ? Dm::NQR : Dm::NQS);
   long long f = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (f >= T.F) return;
+  const BulkTables<R>& BT = bulk<R>(T);
   const long long Z = T.Z, F = T.F;
   FaceInfo fi = face_info(T, f);
   int nq = nq_of<P>(fi.lfg);
   double s2 = T.qpow[fi.k] * T.qpow[fi.k];
   double area = T.A0[6 * fi.cg + fi.lfg] * s2;
-  double mean = phi[f] / area;
+  const R mean = static_cast<R>(phi[f] / area);
+  const R gs = static_cast<R>(fi.gsign);
   int cL = fi.zL >= 0 ? static_cast<int>(fi.zL / T.nr) : -1;
   int cR = fi.zR >= 0 ? static_cast<int>(fi.zR / T.nr) : -1;
-  double b[NQMAX];
-  double wsum = 0.0;
+  R b[NQMAX];
+  R wsum = R(0);
   for (int q = 0; q < nq; ++q) {
     int ig = foff<P>(fi.lfg) + q;
-    const double* nv = T.nF + (static_cast<size_t>(fi.cg) * NQT + ig) * 3;
-    double nx = fi.gsign * nv[0], ny = fi.gsign * nv[1], nz = fi.gsign * nv[2];
-    double bside[2];
+    const R* nv = BT.nF + (static_cast<size_t>(fi.cg) * NQT + ig) * 3;
+    R nx = gs * nv[0], ny = gs * nv[1], nz = gs * nv[2];
+    R bside[2];
     bool have[2] = {false, false};
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
@@ -272,91 +317,97 @@ __global__ void __launch_bounds__(TPB) k_bperp(const DevTables T, const double* 
       int lf = sd == 0 ? fi.lfL : fi.lfR;
       int ql = q;
       if (sd == 1 && fi.se >= 0) ql = T.se_perm[fi.se * Dm::NQS + q];
-      const double* tf = T.TF + (static_cast<size_t>(cc) * NQT + foff<P>(lf) + ql) * NC1;
-      double B[3];
+      const R* tf = BT.TF + (static_cast<size_t>(cc) * NQT + foff<P>(lf) + ql) * NC1;
+      R Bv[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        double s = U[(5 + d) * Z + zz];
+        R s = static_cast<R>(U[(5 + d) * Z + zz]);
 #pragma unroll
         for (int m = 0; m < NC1; ++m) s += tf[m] * Wc[((5 + d) * NC1 + m) * Z + zz];
-        B[d] = s;
+        Bv[d] = s;
       }
-      bside[sd] = nx * B[0] + ny * B[1] + nz * B[2];
+      bside[sd] = nx * Bv[0] + ny * Bv[1] + nz * Bv[2];
       have[sd] = true;
     }
     if (!have[0]) bside[0] = bside[1];
     if (!have[1]) bside[1] = bside[0];
     b[q] = mean + minmod(bside[0] - mean, bside[1] - mean);
-    wsum += T.wF[static_cast<size_t>(fi.cg) * NQT + ig] * b[q];
+    wsum += BT.wF[static_cast<size_t>(fi.cg) * NQT + ig] * b[q];
   }
-  double shift = mean - wsum;
+  R shift = mean - wsum;
   for (int q = 0; q < nq; ++q) Bp[static_cast<size_t>(q) * F + f] = b[q] + shift;
 }
 
 // ----------------------------------------------------------------------------
 // a2 (zone part) + a3: divergence-free B (KKT apply) and the ADER predictor
 // ----------------------------------------------------------------------------
-template <int P>
-__device__ void flux_difference(const DevTables& T, int c, double fs, const double (*Uh)[8], double (*dF)[8]) {
+// dF_i = sum_j sum_alpha D^alpha_ij F^alpha(U_j) - F(U_i).g_i, unscaled by dt (Eq. C.34
+// with the geometric-conservation residual); D^alpha is walked in its sparse
+// column form, so only the nonzero couplings of the serendipity element are formed.
+template <int P, typename R>
+__device__ void flux_difference(const DevTables& T, int c, const R (*Uh)[8], R (*dF)[8]) {
   using Dm = Dim<P>;
   constexpr int N = Dm::N;
-  const double* J0 = T.J0 + static_cast<size_t>(c) * N;
-  const double* Sm = T.Sm + static_cast<size_t>(c) * 9 * N;
-  const double* gc = T.gcl + static_cast<size_t>(c) * N * 3;
-  const double g = T.gamma;
+  const RefConst<P, R>& K = RC<P, R>::get();
+  const BulkTables<R>& B = bulk<R>(T);
+  const R* iJ0 = B.iJ0 + static_cast<size_t>(c) * N;
+  const R* Sm = B.Sm + static_cast<size_t>(c) * 9 * N;
+  const R* gc = B.gcl + static_cast<size_t>(c) * N * 3;
+  const R g = static_cast<R>(T.gamma);
 #pragma unroll 1
   for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) dF[i][v] = 0.0;
+    for (int v = 0; v < 8; ++v) dF[i][v] = R(0);
 #pragma unroll 1
   for (int j = 0; j < N; ++j) {
-    double u[8];
-    double iJ = 1.0 / J0[j];
+    R u[8];
+    const R iJ = iJ0[j];
 #pragma unroll
     for (int v = 0; v < 8; ++v) u[v] = Uh[j][v] * iJ;
-    Prim w = to_prim(u, g);
-    double Fa[3][8];
-#pragma unroll
-    for (int al = 0; al < 3; ++al) {
-      const double* s = Sm + (al * N + j) * 3;
-      flux_n(u, w, s[0], s[1], s[2], Fa[al]);
-    }
-    // geometric-conservation residual at node j
-    double Gj[8];
+    Prim<R> w = to_prim(u, g);
+    R Gj[8];
     flux_n(u, w, gc[3 * j], gc[3 * j + 1], gc[3 * j + 2], Gj);
 #pragma unroll
-    for (int v = 0; v < 8; ++v) dF[j][v] -= fs * Gj[v];
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      double d0 = fs * T.D[(0 * N + i) * N + j];
-      double d1 = fs * T.D[(1 * N + i) * N + j];
-      double d2 = fs * T.D[(2 * N + i) * N + j];
+    for (int v = 0; v < 8; ++v) dF[j][v] -= Gj[v];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) dF[i][v] += d0 * Fa[0][v] + d1 * Fa[1][v] + d2 * Fa[2][v];
+    for (int al = 0; al < 3; ++al) {
+      const R* s = Sm + (al * N + j) * 3;
+      R Fa[8];
+      flux_n(u, w, s[0], s[1], s[2], Fa);
+      const int t0 = K.Dptr[al * (N + 1) + j], t1 = K.Dptr[al * (N + 1) + j + 1];
+#pragma unroll 1
+      for (int t = t0; t < t1; ++t) {
+        const int i = K.Drow[al * Dm::NNZ + t];
+        const R d = K.Dval[al * Dm::NNZ + t];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) dF[i][v] += d * Fa[v];
+      }
     }
   }
 }
 
-template <int P>
+template <int P, typename R>
 __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restrict__ U,
-                                              const double* __restrict__ phi, const double* __restrict__ Wc,
-                                              const double* __restrict__ Bp, double* __restrict__ trF,
-                                              double* __restrict__ trE, double dt) {
+                                              const double* __restrict__ phi, const R* __restrict__ Wc,
+                                              const R* __restrict__ Bp, R* __restrict__ trF,
+                                              R* __restrict__ trE, double dt) {
   using Dm = Dim<P>;
   constexpr int N = Dm::N, M = Dm::M, NC1 = Dm::NC1, NC = Dm::NC, NQT = Dm::NQT, NS = Dm::NS,
                 NBIN = Dm::NBIN;
   long long z = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (z >= T.Z) return;
+  const BulkTables<R>& BT = bulk<R>(T);
+  const RefConst<P, R>& K = RC<P, R>::get();
   const long long Z = T.Z, F = T.F;
   const int nr = T.nr;
   const int c = static_cast<int>(z / nr), k = static_cast<int>(z % nr);
   const double s1 = T.qpow[k];
   const double s2 = s1 * s1;
   // ---- inputs of the divergence-free reconstruction
-  double in[NBIN];
+  R in[NBIN];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    in[d * NC] = U[(5 + d) * Z + z];
+    in[d * NC] = static_cast<R>(U[(5 + d) * Z + z]);
 #pragma unroll
     for (int m = 0; m < NC1; ++m) in[d * NC + 1 + m] = Wc[((5 + d) * NC1 + m) * Z + z];
   }
@@ -374,49 +425,48 @@ __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restr
       f = static_cast<long long>(c) * (nr + 1) + k + (lf == 5 ? 1 : 0);
       sg = lf == 5 ? 1 : -1;
     }
+    const R rsg = static_cast<R>(sg);
     int nq = nq_of<P>(lf);
     for (int q = 0; q < nq; ++q) {
       int ql = q;
       if (lf < 4 && sg < 0) ql = T.se_perm[se * Dm::NQS + q];
-      in[3 * NC + foff<P>(lf) + ql] = sg * Bp[static_cast<size_t>(q) * F + f];
+      in[3 * NC + foff<P>(lf) + ql] = rsg * Bp[static_cast<size_t>(q) * F + f];
     }
-    in[3 * NC + NQT + lf] = sg * phi[f] / (T.A0[6 * c + lf] * s2);
+    in[3 * NC + NQT + lf] = static_cast<R>(sg * phi[f] / (T.A0[6 * c + lf] * s2));
   }
-  const double* GB = T.GB + static_cast<size_t>(c) * (3 + 3 * N) * NBIN;
-  double Uz[8];
+  const R* GB = BT.GB + static_cast<size_t>(c) * (3 + 3 * N) * NBIN;
+  R Uz[8];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) Uz[v] = U[v * Z + z];
+  for (int v = 0; v < 5; ++v) Uz[v] = static_cast<R>(U[v * Z + z]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    double s = 0.0;
+    R s = R(0);
     for (int b = 0; b < NBIN; ++b) s += GB[d * NBIN + b] * in[b];
     Uz[5 + d] = s;
-    U[(5 + d) * Z + z] = s;  // Sec. IV.b step 10: zone B <- divergence-free mean
+    U[(5 + d) * Z + z] = static_cast<double>(s);  // Sec. IV.b step 10: zone B <- divergence-free mean
   }
   // ---- initial nodal states U_hat_1 = J U(x_i)
-  double Uh[M][N][8];
-  const double* TN = T.TN + static_cast<size_t>(c) * N * NC1;
-  const double* J0 = T.J0 + static_cast<size_t>(c) * N;
+  R Uh[M][N][8];
+  const R* TN = BT.TN + static_cast<size_t>(c) * N * NC1;
+  const R* J0 = BT.J0 + static_cast<size_t>(c) * N;
 #pragma unroll 1
   for (int i = 0; i < N; ++i) {
-    double u[8];
+    R u[8];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double s = Uz[v];
+      R s = Uz[v];
       for (int m = 0; m < NC1; ++m) s += TN[i * NC1 + m] * Wc[(v * NC1 + m) * Z + z];
       u[v] = s;
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double* row = GB + (3 + d * N + i) * NBIN;
-      double s = 0.0;
+      const R* row = GB + (3 + d * N + i) * NBIN;
+      R s = R(0);
       for (int b = 0; b < NBIN; ++b) s += row[b] * in[b];
       u[5 + d] = s;
     }
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      Uh[0][i][v] = J0[i] * u[v];
-    }
+    for (int v = 0; v < 8; ++v) Uh[0][i][v] = J0[i] * u[v];
   }
 #pragma unroll 1
   for (int m = 1; m < M; ++m)
@@ -425,82 +475,99 @@ __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restr
 #pragma unroll
       for (int v = 0; v < 8; ++v) Uh[m][i][v] = Uh[0][i][v];
   // ---- Picard iterations (Eqs. C.34-C.36)
-  const double fs = dt / s1;  // dt * l_0 / l_k (Eq. 5.21)
-  double dF1[N][8];
-  double dFm[M - 1][N][8];
-  flux_difference<P>(T, c, fs, Uh[0], dF1);
+  const R fs = static_cast<R>(dt / s1);  // dt * l_0 / l_k (Eq. 5.21)
+  R dF1[N][8];
+  R dFm[M - 1][N][8];
+  flux_difference<P, R>(T, c, Uh[0], dF1);
 #pragma unroll 1
   for (int it = 0; it < P; ++it) {
 #pragma unroll 1
-    for (int m = 1; m < M; ++m) flux_difference<P>(T, c, fs, Uh[m], dFm[m - 1]);
+    for (int m = 1; m < M; ++m) flux_difference<P, R>(T, c, Uh[m], dFm[m - 1]);
 #pragma unroll 1
     for (int kk = 1; kk < M; ++kk) {
-      double r0 = T.R[kk * M];
+      R rk[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) rk[m] = fs * K.R_[kk * M + m];
 #pragma unroll 1
       for (int i = 0; i < N; ++i)
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-          double s = Uh[0][i][v] - r0 * dF1[i][v];
-          for (int m = 1; m < M; ++m) s -= T.R[kk * M + m] * dFm[m - 1][i][v];
+          R s = Uh[0][i][v] - rk[0] * dF1[i][v];
+#pragma unroll
+          for (int m = 1; m < M; ++m) s -= rk[m] * dFm[m - 1][i][v];
           Uh[kk][i][v] = s;
         }
     }
   }
-  // ---- traces at the zone's face and edge points, Gauss times tau_2..tau_M
-  const double* JF = T.JF + static_cast<size_t>(c) * NQT;
+  // ---- traces at the zone's face and edge points, Gauss times tau_2..tau_M;
+  // a face (edge) point only sees the nodes of its face (edge)
+  const R* JF = BT.JF + static_cast<size_t>(c) * NQT;
 #pragma unroll 1
   for (int m = 1; m < M; ++m)
 #pragma unroll 1
-    for (int idx = 0; idx < NQT; ++idx) {
-      const double* ps = T.psiF + static_cast<size_t>(idx) * N;
-      double acc[8];
+    for (int lf = 0; lf < 6; ++lf) {
+      const int nq = nq_of<P>(lf), f0 = foff<P>(lf);
+#pragma unroll 1
+      for (int q = 0; q < nq; ++q) {
+        const int idx = f0 + q;
+        R acc[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) acc[v] = 0.0;
-      for (int i = 0; i < N; ++i) {
-        double w = ps[i];
+        for (int v = 0; v < 8; ++v) acc[v] = R(0);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[v] += w * Uh[m][i][v];
+        for (int a = 0; a < Dm::NFN; ++a) {
+          const R w = K.psiFc[idx * Dm::NFN + a];
+          const int i = K.fnode[lf * Dm::NFN + a];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[v] += w * Uh[m][i][v];
+        }
+        const R iJ = R(1) / JF[idx];
+        R* out = trF + (static_cast<size_t>((m - 1) * NQT + idx) * 8) * Z + z;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) out[v * Z] = acc[v] * iJ;
       }
-      double iJ = 1.0 / JF[idx];
-      double* out = trF + (static_cast<size_t>((m - 1) * NQT + idx) * 8) * Z + z;
-#pragma unroll
-      for (int v = 0; v < 8; ++v) out[v * Z] = acc[v] * iJ;
     }
-  const double* JE = T.JE + static_cast<size_t>(c) * 12 * NS;
+  const R* JE = BT.JE + static_cast<size_t>(c) * 12 * NS;
 #pragma unroll 1
   for (int m = 1; m < M; ++m)
 #pragma unroll 1
-    for (int idx = 0; idx < 12 * NS; ++idx) {
-      const double* ps = T.psiE + static_cast<size_t>(idx) * N;
-      double acc[8];
+    for (int le = 0; le < 12; ++le)
+#pragma unroll 1
+      for (int s = 0; s < NS; ++s) {
+        const int idx = le * NS + s;
+        R acc[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) acc[v] = 0.0;
-      for (int i = 0; i < N; ++i) {
-        double w = ps[i];
+        for (int v = 0; v < 8; ++v) acc[v] = R(0);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[v] += w * Uh[m][i][v];
+        for (int a = 0; a < Dm::NEN; ++a) {
+          const R w = K.psiEc[idx * Dm::NEN + a];
+          const int i = K.enode[le * Dm::NEN + a];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[v] += w * Uh[m][i][v];
+        }
+        const R iJ = R(1) / JE[idx];
+        R* out = trE + (static_cast<size_t>((m - 1) * 12 * NS + idx) * 8) * Z + z;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) out[v * Z] = acc[v] * iJ;
       }
-      double iJ = 1.0 / JE[idx];
-      double* out = trE + (static_cast<size_t>((m - 1) * 12 * NS + idx) * 8) * Z + z;
-#pragma unroll
-      for (int v = 0; v < 8; ++v) out[v * Z] = acc[v] * iJ;
-    }
 }
 
 // ----------------------------------------------------------------------------
-// a4: face fluxes (HLL at face points x Gauss times)
+// a4: face fluxes (HLL at face points x Gauss times, FP64 accumulation)
 // ----------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const double* __restrict__ trF,
+template <int P, typename R>
+__global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* __restrict__ trF,
                                                    double* __restrict__ Ff, double dt) {
   using Dm = Dim<P>;
   constexpr int M = Dm::M, NQT = Dm::NQT;
   long long f = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (f >= T.F) return;
+  const BulkTables<R>& BT = bulk<R>(T);
   const long long Z = T.Z, F = T.F;
   FaceInfo fi = face_info(T, f);
   int nq = nq_of<P>(fi.lfg);
   double s2 = T.qpow[fi.k] * T.qpow[fi.k];
+  const R gs = static_cast<R>(fi.gsign);
+  const R g = static_cast<R>(T.gamma);
   double acc[8];
 #pragma unroll
   for (int v = 0; v < 8; ++v) acc[v] = 0.0;
@@ -510,19 +577,19 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const doub
 #pragma unroll 1
     for (int q = 0; q < nq; ++q) {
       int ig = foff<P>(fi.lfg) + q;
-      const double* nv = T.nF + (static_cast<size_t>(fi.cg) * NQT + ig) * 3;
-      double nx = fi.gsign * nv[0], ny = fi.gsign * nv[1], nz = fi.gsign * nv[2];
+      const R* nv = BT.nF + (static_cast<size_t>(fi.cg) * NQT + ig) * 3;
+      R nx = gs * nv[0], ny = gs * nv[1], nz = gs * nv[2];
       double W = wt * T.WF[static_cast<size_t>(fi.cg) * NQT + ig] * s2;
-      double uL[8], uR[8];
+      R uL[8], uR[8];
       if (fi.zL >= 0) {
-        const double* src = trF + (static_cast<size_t>((m - 1) * NQT + foff<P>(fi.lfL) + q) * 8) * Z + fi.zL;
+        const R* src = trF + (static_cast<size_t>((m - 1) * NQT + foff<P>(fi.lfL) + q) * 8) * Z + fi.zL;
 #pragma unroll
         for (int v = 0; v < 8; ++v) uL[v] = src[v * Z];
       }
       if (fi.zR >= 0) {
         int ql = q;
         if (fi.se >= 0) ql = T.se_perm[fi.se * Dm::NQS + q];
-        const double* src = trF + (static_cast<size_t>((m - 1) * NQT + foff<P>(fi.lfR) + ql) * 8) * Z + fi.zR;
+        const R* src = trF + (static_cast<size_t>((m - 1) * NQT + foff<P>(fi.lfR) + ql) * 8) * Z + fi.zR;
 #pragma unroll
         for (int v = 0; v < 8; ++v) uR[v] = src[v * Z];
       }
@@ -534,7 +601,7 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const doub
 #pragma unroll
         for (int v = 0; v < 8; ++v) uR[v] = uL[v];
       }
-      hll_acc(uL, uR, nx, ny, nz, T.gamma, W, acc);
+      hll_acc(uL, uR, nx, ny, nz, g, W, acc);
     }
   }
 #pragma unroll
@@ -542,10 +609,11 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const doub
 }
 
 // ----------------------------------------------------------------------------
-// a5: edge EMFs (multidimensional Rusanov at edge points x Gauss times)
+// a5: edge EMFs (multidimensional Rusanov at edge points x Gauss times, FP64
+// accumulation)
 // ----------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const double* __restrict__ trE,
+template <int P, typename R>
+__global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __restrict__ trE,
                                                   double* __restrict__ Ee, double dt) {
   using Dm = Dim<P>;
   constexpr int M = Dm::M, NS = Dm::NS;
@@ -553,7 +621,7 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const doubl
   if (e >= T.E) return;
   const long long Z = T.Z;
   const int nr = T.nr;
-  const double g = T.gamma;
+  const R g = static_cast<R>(T.gamma);
   long long zs[4];
   int les[4], revs[4];
   int nz = 0, nf = 0;
@@ -607,39 +675,40 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const doubl
       dlw[s] = T.se_dlw[se * NS + s] * T.qpow[kk];
     }
   }
+  const R inz = R(1) / static_cast<R>(nz);
   double acc = 0.0;
 #pragma unroll 1
   for (int m = 1; m < M; ++m) {
     double wt = T.wt[m - 1];
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
-      double st[4][8];
+      R st[4][8];
       for (int j = 0; j < nz; ++j) {
         int sl = revs[j] ? NS - 1 - s : s;
-        const double* src = trE + (static_cast<size_t>((m - 1) * 12 * NS + les[j] * NS + sl) * 8) * Z + zs[j];
+        const R* src = trE + (static_cast<size_t>((m - 1) * 12 * NS + les[j] * NS + sl) * 8) * Z + zs[j];
 #pragma unroll
         for (int v = 0; v < 8; ++v) st[j][v] = src[v * Z];
       }
-      double tx = tv[s][0], ty = tv[s][1], tz = tv[s][2];
-      double E = 0.0;
+      R tx = static_cast<R>(tv[s][0]), ty = static_cast<R>(tv[s][1]), tz = static_cast<R>(tv[s][2]);
+      R E = R(0);
       for (int j = 0; j < nz; ++j) {
-        double ir = 1.0 / st[j][0];
-        double vx = st[j][1] * ir, vy = st[j][2] * ir, vz = st[j][3] * ir;
-        double bx = st[j][5], by = st[j][6], bz = st[j][7];
+        R ir = R(1) / st[j][0];
+        R vx = st[j][1] * ir, vy = st[j][2] * ir, vz = st[j][3] * ir;
+        R bx = st[j][5], by = st[j][6], bz = st[j][7];
         // (-v x B) . t
         E -= (vy * bz - vz * by) * tx + (vz * bx - vx * bz) * ty + (vx * by - vy * bx) * tz;
       }
       for (int j = 0; j < nf; ++j) {
-        const double* nv = fn[j] + 3 * s;
-        double a = fmax(rusanov_speed(st[fL[j]], nv[0], nv[1], nv[2], g),
-                        rusanov_speed(st[fR[j]], nv[0], nv[1], nv[2], g));
+        const double* nvd = fn[j] + 3 * s;
+        R nx = static_cast<R>(nvd[0]), ny = static_cast<R>(nvd[1]), nzz = static_cast<R>(nvd[2]);
+        R a = fmax(rusanov_speed(st[fL[j]], nx, ny, nzz, g), rusanov_speed(st[fR[j]], nx, ny, nzz, g));
         // t x n
-        double cx = ty * nv[2] - tz * nv[1], cy = tz * nv[0] - tx * nv[2], cz = tx * nv[1] - ty * nv[0];
-        double dbx = st[fR[j]][5] - st[fL[j]][5], dby = st[fR[j]][6] - st[fL[j]][6],
-               dbz = st[fR[j]][7] - st[fL[j]][7];
+        R cx = ty * nzz - tz * ny, cy = tz * nx - tx * nzz, cz = tx * ny - ty * nx;
+        R dbx = st[fR[j]][5] - st[fL[j]][5], dby = st[fR[j]][6] - st[fL[j]][6],
+          dbz = st[fR[j]][7] - st[fL[j]][7];
         E += a * (dbx * cx + dby * cy + dbz * cz);
       }
-      acc += wt * dlw[s] * (E / nz);
+      acc += wt * dlw[s] * static_cast<double>(E * inz);
     }
   }
   Ee[e] = dt * acc;
@@ -885,9 +954,67 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
   return cudaGetLastError();
 }
 
-template cudaError_t launch_stage<2>(int, const DevTables&, const DevState&, double, cudaStream_t);
-template cudaError_t launch_stage<3>(int, const DevTables&, const DevState&, double, cudaStream_t);
-template cudaError_t launch_stage<4>(int, const DevTables&, const DevState&, double, cudaStream_t);
+template <int P, typename R>
+cudaError_t upload_reference_constants(const Tables& T) {
+  using Dm = Dim<P>;
+  RefConst<P, R> h{};
+  for (int i = 0; i < 3 * Dm::NNZ; ++i) {
+    h.Dval[i] = static_cast<R>(T.Dval[i]);
+    h.Drow[i] = static_cast<unsigned char>(T.Drow[i]);
+  }
+  for (int i = 0; i < 3 * (Dm::N + 1); ++i) h.Dptr[i] = static_cast<unsigned short>(T.Dptr[i]);
+  for (int i = 0; i < Dm::NQT * Dm::NFN; ++i) h.psiFc[i] = static_cast<R>(T.psiFc[i]);
+  for (int i = 0; i < 6 * Dm::NFN; ++i) h.fnode[i] = static_cast<unsigned char>(T.fnode[i]);
+  for (int i = 0; i < 12 * Dm::NS * Dm::NEN; ++i) h.psiEc[i] = static_cast<R>(T.psiEc[i]);
+  for (int i = 0; i < 12 * Dm::NEN; ++i) h.enode[i] = static_cast<unsigned char>(T.enode[i]);
+  for (int i = 0; i < Dm::M * Dm::M; ++i) h.R_[i] = static_cast<R>(T.R[i]);
+  return cudaMemcpyToSymbol(RC<P, R>::sym(), &h, sizeof(h));
+}
+
+template <int P, typename R>
+cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, double dt, cudaStream_t st) {
+  R* Wc = static_cast<R*>(S.Wc);
+  R* Bp = static_cast<R*>(S.Bp);
+  R* trF = static_cast<R*>(S.trF);
+  R* trE = static_cast<R*>(S.trE);
+  switch (stage) {
+    case ST_WENO:
+      k_weno<P, R><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, Wc);
+      break;
+    case ST_BPERP:
+      k_bperp<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp);
+      break;
+    case ST_ADER:
+      k_ader<P, R><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+      break;
+    case ST_FACE:
+      k_face_flux<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, trF, S.Ff, dt);
+      break;
+    case ST_EDGE:
+      k_edge_emf<P, R><<<grid_for(T.E), TPB, 0, st>>>(T, trE, S.Ee, dt);
+      break;
+    case ST_UPD_U:
+      k_update_u<<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.Ff);
+      break;
+    case ST_UPD_PHI:
+      k_update_phi<<<grid_for(T.F), TPB, 0, st>>>(T, S.phi, S.Ee);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+#define GEO_INSTANTIATE(P, R)                                                                       \
+  template cudaError_t upload_reference_constants<P, R>(const Tables&);                              \
+  template cudaError_t launch_stage<P, R>(int, const DevTables&, const DevState&, double, cudaStream_t);
+GEO_INSTANTIATE(2, double)
+GEO_INSTANTIATE(3, double)
+GEO_INSTANTIATE(4, double)
+GEO_INSTANTIATE(2, float)
+GEO_INSTANTIATE(3, float)
+GEO_INSTANTIATE(4, float)
+#undef GEO_INSTANTIATE
 
 cudaError_t launch_cfl(const DevTables& T, const DevState& S, double cfl, double* out_host, cudaStream_t st) {
   int nb = reduction_blocks(T.Z);

@@ -46,7 +46,7 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("n,nr,p", [(5, 3, 2), (4, 4, 3)])
+@pytest.mark.parametrize("n,nr,p", [(5, 3, 2), (4, 4, 3), (3, 5, 4)])
 def test_stages_match_oracle(n, nr, p):
     from paper_1905_02504_gb300 import geomhd
     o, m, U, phi = setup_case(n, nr, p)
@@ -94,7 +94,7 @@ def test_stages_match_oracle(n, nr, p):
     m.close()
 
 
-@pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 10), (4, 4, 3, 4)])
+@pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 10), (4, 4, 3, 4), (3, 5, 4, 2)])
 def test_multistep_parity_and_divb(n, nr, p, steps):
     o, m, U, phi = setup_case(n, nr, p)
     dt = o.cfl_dt(U, 0.4)
@@ -110,9 +110,9 @@ def test_multistep_parity_and_divb(n, nr, p, steps):
     m.close()
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [2, 3, 4])
 def test_free_stream_on_gpu(p):
-    o, m, U, phi = setup_case(4, 3, p, problem="uniform")
+    o, m, U, phi = setup_case(4 if p < 4 else 3, 3 if p < 4 else 5, p, problem="uniform")
     dt = m.cfl_dt(0.3)
     for _ in range(3):
         m.step(dt)
