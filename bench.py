@@ -179,16 +179,17 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
-def captured_traffic(a, kernel, Z):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu capture,
-    scaled by zones; None when the kernel source changed since the capture."""
+def captured_traffic(a, kernel, Z, prec="fp64"):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu capture
+    (a smaller case of the same kernel), scaled by zones; None when the kernel
+    source changed since the capture."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")))
         src = open(os.path.join(ROOT, "paper_1905_02504_gb300", "csrc", "kernels.cu"), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != rec["kernels_cu_sha256_prefix"] or rec["order"] != a.order:
             return None
-        return rec["dram_bytes_per_zone"] * Z
+        return rec["dram_bytes_per_zone"][prec] * Z
     except (OSError, KeyError, ValueError):
         return None
 
@@ -242,7 +243,9 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "value": ws * m32.Z * a.steps / (t_ms * 1e-3), "unit": "zone-updates/s",
         "ms_per_step": t_ms / a.steps, "dtype": "f32 bulk / f64 accumulation and updates",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
-                     "frac": achieved / nominal_fp32, "traffic": None, "kernel": "k_" + geomhd.STAGES[top],
+                     "frac": achieved / nominal_fp32,
+                     "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], m32.Z, "fp32"),
+                     "kernel": "k_" + geomhd.STAGES[top],
                      "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
                                   "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
                      "measured_fp32_fma_tflops": fp32_probe},
