@@ -36,6 +36,8 @@ from .mesh import taylor_exponents
 
 
 def minmod(a, b):
+    from . import physics
+    physics.record("minmod", np.stack([a * b > 0.0, np.abs(a) <= np.abs(b)]))
     return np.where(a * b > 0.0, np.sign(a) * np.minimum(np.abs(a), np.abs(b)), 0.0)
 
 

@@ -25,6 +25,15 @@ import numpy as np
 
 RHO, MX, MY, MZ, EN, BX, BY, BZ = range(8)
 
+# Optional branch recorder (tests use it to detect finite-difference stencils that
+# cross a MinMod / HLL / max switch): a list that the branchy routines append to.
+BRANCHES = None
+
+
+def record(tag, arr):
+    if BRANCHES is not None:
+        BRANCHES.append((tag, np.asarray(arr).copy()))
+
 
 def primitives(U, gamma):
     rho = U[..., RHO]
@@ -80,6 +89,7 @@ def hll(UL, UR, nhat, gamma):
     Fs = (SR[..., None] * FL - SL[..., None] * FR
           + (SL * SR)[..., None] * (UR - UL)) / (SR - SL)[..., None]
     out = np.where((SL >= 0.0)[..., None], FL, np.where((SR <= 0.0)[..., None], FR, Fs))
+    record("hll", np.stack([SL >= 0.0, SR <= 0.0, vnL - cL <= vnR - cR, vnL + cL >= vnR + cR]))
     return out
 
 
@@ -99,6 +109,8 @@ def edge_emf(states, faces, tvec, gamma):
     E = -np.cross(v, B)
     acc = (E @ tvec).sum()
     for iL, iR, nh in faces:
-        a = max(rusanov_speed(states[iL], nh, gamma), rusanov_speed(states[iR], nh, gamma))
+        aL, aR = rusanov_speed(states[iL], nh, gamma), rusanov_speed(states[iR], nh, gamma)
+        record("emf", [aL >= aR, (states[iL][MX:MZ + 1] @ nh) >= 0.0, (states[iR][MX:MZ + 1] @ nh) >= 0.0])
+        a = max(aL, aR)
         acc += a * np.dot(B[iR] - B[iL], np.cross(tvec, nh))
     return acc / k

@@ -29,7 +29,7 @@ the exact advected entropy wave.
 """
 import numpy as np
 
-from . import quadrature
+from . import positivity, quadrature
 from .ader import AderPredictor
 from .divfree import DivFreeB
 from .mesh import Mesh
@@ -38,8 +38,9 @@ from .weno import WenoAO
 
 
 class Oracle:
-    def __init__(self, n, nr, r_in, r_out, p, gamma=5.0 / 3.0):
+    def __init__(self, n, nr, r_in, r_out, p, gamma=5.0 / 3.0, positivity=False):
         self.gamma = gamma
+        self.positivity = positivity
         m = self.mesh = Mesh(n, nr, r_in, r_out, p)
         self.weno = WenoAO(m)
         self.dfb = DivFreeB(m, self.weno)
@@ -134,9 +135,25 @@ class Oracle:
         Unodes = np.empty(X.shape[:2] + (8,))
         Unodes[..., :5] = self.weno.evaluate(coeffs, U1, X)[..., :5]
         Unodes[..., 5:8] = self.dfb.evaluate(Bcoef, X)
+        if self.positivity:
+            Unodes, _ = positivity.limit(Unodes, U1, g)
         Uh = self.ader.predict(Unodes, dt)
         # ---- face fluxes
         traces = [self.ader.point_values(Uh, self.face_ref[lf]) for lf in range(6)]
+        t, w = quadrature.edge_rule(p)
+        edge_traces = [self.ader.point_values(Uh, refelem.edge_points(le, t)) for le in range(12)]
+        if self.positivity:
+            # one scaling per zone over every predicted face / edge point and Gauss time
+            parts = [tr[:, 1:].reshape(m.Z, -1, 8) for tr in traces + edge_traces]
+            sizes = [x.shape[1] for x in parts]
+            lim, _ = positivity.limit(np.concatenate(parts, axis=1), U1, g)
+            out, off = [], 0
+            for tr, sz in zip(traces + edge_traces, sizes):
+                new = tr.copy()
+                new[:, 1:] = lim[:, off:off + sz].reshape(tr[:, 1:].shape)
+                out.append(new)
+                off += sz
+            traces, edge_traces = out[:6], out[6:]
         Fface = np.zeros((m.F, 8))
         fg = self.dfb.fgeo
         for f in range(m.F):
@@ -161,8 +178,6 @@ class Oracle:
                 Fq = hll(sL, sR, n, g)
                 Fface[f] += dt * self.wt[mi - 1] * (W[:, None] * Fq).sum(0)
         # ---- edge EMFs
-        t, w = quadrature.edge_rule(p)
-        edge_traces = [self.ader.point_values(Uh, refelem.edge_points(le, t)) for le in range(12)]
         Eedge = np.zeros(m.E)
         for (kz, kf), items in self.edge_groups.items():
             for e, slots, fl, x0, tv, dl in items:
