@@ -43,14 +43,39 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
     ap.add_argument("--compare-steps", type=int, default=10)
+    ap.add_argument("--problem", default="smooth", choices=["smooth", "blast", "lowbeta"])
+    ap.add_argument("--noise", type=float, default=0.0, help="seeded relative density noise")
+    ap.add_argument("--positivity", action="store_true")
+    ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-bulk form")
+    ap.add_argument("--cfl-every-step", action="store_true",
+                    help="device CFL reduction before every timed step (dt read back each step)")
+    ap.add_argument("--nq-zone", type=int, default=0, help="cubature points per direction for the initial data")
+    ap.add_argument("--nq-edge", type=int, default=8, help="Gauss points per edge for the initial face fluxes")
+    ap.add_argument("--predictor", type=int, default=None, choices=[0, 1],
+                    help="predictor schedule: 0 one thread per zone, 1 one thread per node (default: per form)")
     ap.add_argument("--sample-n", type=int, default=4)
     ap.add_argument("--sample-nr", type=int, default=4)
     return ap.parse_args()
 
 
 def workload_name(a):
-    return "cubed-sphere %dx%dx%d x %d shells (%d zones), order %d, FP64, smooth test" % (
-        6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order)
+    form = "FP32-bulk" if getattr(a, "fp32_only", False) else "FP64"
+    extra = ""
+    if getattr(a, "positivity", False):
+        extra += ", positivity on"
+    if getattr(a, "noise", 0.0):
+        extra += ", density noise %g" % a.noise
+    if getattr(a, "cfl_every_step", False):
+        extra += ", device CFL every step"
+    return "cubed-sphere %dx%dx%d x %d shells (%d zones), order %d, %s, %s test%s" % (
+        6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order, form, getattr(a, "problem", "smooth"), extra)
+
+
+def sched_name(pred, fp32):
+    """Predictor schedule in use: the library default is per form."""
+    if pred is None:
+        pred = 1 if fp32 else 0
+    return "node-team" if pred == 1 else "zone-thread"
 
 
 def dist_env():
@@ -123,8 +148,8 @@ import json, os, sys, time
 sys.path.insert(0, %(root)r)
 from oracle.step import Oracle
 from paper_1905_02504_gb300.inputs import make_problem
-o = Oracle(%(n)d, %(nr)d, 1.0, 2.0, %(p)d)
-U, phi = o.initial_state(make_problem("smooth"))
+o = Oracle(%(n)d, %(nr)d, 1.0, 2.0, %(p)d, positivity=%(pos)r)
+U, phi = o.initial_state(make_problem(%(problem)r, noise=%(noise)r))
 dt = o.cfl_dt(U, %(cfl)r)
 times = []
 for s in range(%(steps)d):
@@ -135,11 +160,12 @@ print(json.dumps({"Z": o.mesh.Z, "times": times}))
 """
 
 
-def run_oracle(n, nr, p, cfl, steps):
+def run_oracle(n, nr, p, cfl, steps, problem="smooth", noise=0.0, pos=False):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET % dict(root=ROOT, n=n, nr=nr, p=p, cfl=cfl, steps=steps)
+    code = ORACLE_SNIPPET % dict(root=ROOT, n=n, nr=nr, p=p, cfl=cfl, steps=steps, problem=problem,
+                                 noise=noise, pos=bool(pos))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3000)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -147,19 +173,20 @@ def run_oracle(n, nr, p, cfl, steps):
 
 
 def cpu_baseline(a):
-    res = run_oracle(a.sample_n, a.sample_nr, a.order, a.cfl, 1)
+    res = run_oracle(a.sample_n, a.sample_nr, a.order, a.cfl, 1, a.problem, a.noise, a.positivity)
     t = sum(res["times"])
     return {"value": res["Z"] / t, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
-            "sample": "1 FP64 oracle step of the same order-%d smooth test on the 6x%dx%dx%d mesh "
+            "sample": "1 FP64 oracle step of the same order-%d %s test on the 6x%dx%dx%d mesh "
                       "(%d zones), single thread, mesh setup excluded" % (
-                          a.order, a.sample_n, a.sample_n, a.sample_nr, res["Z"])}
+                          a.order, a.problem, a.sample_n, a.sample_n, a.sample_nr, res["Z"])}
 
 
 def reference_arm(a):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    res = run_oracle(a.sample_n, a.sample_nr, a.order, a.cfl, a.warmup + a.steps)
+    res = run_oracle(a.sample_n, a.sample_nr, a.order, a.cfl, a.warmup + a.steps, a.problem, a.noise,
+                     a.positivity)
     times = res["times"][a.warmup:]
     Z = res["Z"]
     total = sum(times)
@@ -171,9 +198,9 @@ def reference_arm(a):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "sample_zones": Z},
         "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": "each step: one FP64 oracle step of the order-%d smooth test on "
+                         "sample": "each step: one FP64 oracle step of the order-%d %s test on "
                                    "the 6x%dx%dx%d mesh (%d zones), single thread" % (
-                                       a.order, a.sample_n, a.sample_n, a.sample_nr, Z)},
+                                       a.order, a.problem, a.sample_n, a.sample_n, a.sample_nr, Z)},
         "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -204,6 +231,10 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
     from paper_1905_02504_gb300 import geomhd
     sid = stream.cuda_stream
     m32 = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, prec=geomhd.GEO_FP32_BULK, stream=sid)
+    if a.predictor is not None:
+        geomhd.geo_set_predictor(m32.h, a.predictor)
+    if a.positivity:
+        geomhd.geo_set_positivity(m32.h, 1)
     m32.upload(U0, phi0)
     with torch.cuda.stream(stream):
         for _ in range(a.warmup):
@@ -252,6 +283,7 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "stages": {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
                    for s in range(geomhd.N_STAGES)},
         "rel_l1_vs_fp64": err, "rel_l1_phi_vs_fp64": errp, "steps_compared": a.compare_steps,
+        "predictor": sched_name(a.predictor, True),
         "divB_rel": r32,
     }
     m32.close()
@@ -274,8 +306,14 @@ def gpu_arm(a):
 
     stream = torch.cuda.Stream()
     sid = stream.cuda_stream
-    mesh = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, stream=sid)
-    U0, phi0 = mesh.initial_state(make_problem("smooth"))
+    prec = geomhd.GEO_FP32_BULK if a.fp32_only else geomhd.GEO_FP64
+    mesh = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, prec=prec, stream=sid)
+    if a.predictor is not None:
+        geomhd.geo_set_predictor(mesh.h, a.predictor)
+    if a.positivity:
+        geomhd.geo_set_positivity(mesh.h, 1)
+    U0, phi0 = mesh.initial_state(make_problem(a.problem, noise=a.noise), nq_zone=a.nq_zone or None,
+                                  nq_edge=a.nq_edge)
     mesh.upload(U0, phi0)
     dt = mesh.cfl_dt(a.cfl)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -299,6 +337,8 @@ def gpu_arm(a):
         for i in range(a.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
+            if a.cfl_every_step:
+                dt = mesh.cfl_dt(a.cfl)
             mesh.step(dt)
             ev[i][1].record(stream)
     barrier()
@@ -330,6 +370,7 @@ def gpu_arm(a):
     barrier()
     t_e2e = time.perf_counter() - t0
     e2e_value = ws * Z * e2e_steps / t_e2e
+    finite = bool(torch.isfinite(Uo).all().item() and torch.isfinite(po).all().item())
     bytes_state = (Uh.numel() + ph.numel()) * 8
 
     # ---- roofline of the dominant kernel (plain FP64 ALU work)
@@ -337,31 +378,43 @@ def gpu_arm(a):
     avg = stage_ms / np.maximum(stage_cnt, 1)
     top = int(np.argmax(avg))
     achieved = flops[top] * units[top] / (avg[top] * 1e-3) / 1e12
-    fma_peak = geomhd.geo_probe_fma_peak(0, sid) / 1e12
-    nominal_fp64 = 1.25
-    roofline = {"bound": "alu", "achieved": achieved, "peak": nominal_fp64, "unit": "TFLOP/s",
-                "frac": achieved / nominal_fp64, "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], Z),
-                "kernel": "k_" + geomhd.STAGES[top],
-                "peak_kind": "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak,
-                "measured_fp64_fma_tflops": fma_peak}
+    if a.fp32_only:
+        fma_peak = geomhd.geo_probe_fma_peak(1, sid) / 1e12
+        nominal = 152 * 128 * 2 * 2.07e9 / 1e12
+        kind = ("nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 FMA-chain probe "
+                "%.1f TFLOP/s" % fma_peak)
+    else:
+        fma_peak = geomhd.geo_probe_fma_peak(0, sid) / 1e12
+        nominal = 1.25
+        kind = "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak
+    roofline = {"bound": "alu", "achieved": achieved, "peak": nominal, "unit": "TFLOP/s",
+                "frac": achieved / nominal,
+                "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], Z, "fp32" if a.fp32_only else "fp64"),
+                "kernel": "k_" + geomhd.STAGES[top], "peak_kind": kind, "measured_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
-    fp32 = None if a.no_fp32 else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
+    fp32 = None if (a.no_fp32 or a.fp32_only) else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_ms / a.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-bulk" if a.fp32_only else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(a), "zones": Z, "order": a.order, "dt": dt,
+                       "problem": a.problem, "positivity": a.positivity,
+                       "predictor": sched_name(a.predictor, a.fp32_only),
                        "cfl": a.cfl, "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "gpu_launches": int(geomhd.N_STAGES * a.steps),
+            # per step: the seven stage kernels, the trace positivity kernel when the
+            # limiter is on, the two-kernel CFL reduction when dt is recomputed
+            "gpu_launches": int((geomhd.N_STAGES + int(a.positivity) + 2 * int(a.cfl_every_step)) * a.steps),
             "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": bytes_state,
                     "d2h_bytes_per_step": bytes_state},
             "roofline": roofline,
             "stages": stages,
             "divB_rel": r_div,
+            "state_finite": finite,
             "clocks": clocks,
         }
         if fp32 is not None:

@@ -89,6 +89,26 @@ int geo_mesh_sizes(geo_mesh_t mesh, int64_t* n_zones, int64_t* n_faces, int64_t*
 /* Ratio gamma of specific heats (default 5/3). */
 int geo_set_gamma(geo_mesh_t mesh, double gamma);
 
+/* Positivity limiting (paper Sec. I: WENO "ruggedized" to be positivity
+ * preserving; details not in the paper).  When enabled, every step scales the
+ * zone's initial nodal states of the predictor, and then all its predicted
+ * face/edge point states, toward the zone mean by one factor theta <= 1 so that
+ * density and pressure stay >= min(1e-13, zone mean) at those points (Zhang-Shu
+ * type scaling; the pressure bound uses the concavity of p).  Default: off. */
+int geo_set_positivity(geo_mesh_t mesh, int enable);
+
+/* Execution schedule of the predictor stage (a2 zone part + a3, Sec. IV.b steps
+ * 8-10 and Eqs. C.34-C.36); both compute the same arithmetic:
+ *   GEO_PRED_ZONE_THREAD (0): one thread per zone, its nodal states in
+ *     thread-local memory (default of the FP64 form);
+ *   GEO_PRED_NODE_TEAM (1): one thread per serendipity node, a team of N threads
+ *     per zone exchanging nodal fluxes through shared memory (default of the
+ *     FP32-bulk form).
+ * The two differ only in the summation order of the flux-difference rows.
+ * Returns GEO_ERR_ARG for any other value. */
+enum { GEO_PRED_ZONE_THREAD = 0, GEO_PRED_NODE_TEAM = 1 };
+int geo_set_predictor(geo_mesh_t mesh, int schedule);
+
 /* Zone cubature for initial data (host buffers, caller-owned):
  * pts double[Z][nq^3][3] physical points, w double[Z][nq^3] physical weights
  * (Jacobian included, summing to the zone volume); nq in 1..12 points per
@@ -129,6 +149,23 @@ int geo_step(geo_mesh_t mesh, double dt);
 /* Discrete divergence of the face fluxes (paper Sec. II.c): per zone
  * sum_f s_zf phi_f; returns max |.| and max |.| / sum_f |phi_f| (synchronises). */
 int geo_divB_max(geo_mesh_t mesh, double* abs_max, double* rel_max);
+
+/* Adjoint of one step for fixed dt (no counterpart in the paper: a hand-written
+ * reverse sweep of every stage of geo_step, Sec. VI; MinMod and the Riemann
+ * solvers follow the branch the forward step took).  All pointers are device
+ * pointers (caller-owned): U_in double[8][Z] and phi_in double[F] are the state
+ * at t (the checkpoint; the step is recomputed from it), gU_out / gphi_out the
+ * cotangent at t + dt; gU_in / gphi_in receive the cotangent at t.  Only for
+ * GEO_FP64 meshes (GEO_ERR_ARG otherwise).  The mesh's own state is untouched;
+ * work buffers are allocated on the first call.  Asynchronous on the mesh stream. */
+int geo_step_adjoint(geo_mesh_t mesh, double dt, const double* U_in, const double* phi_in,
+                     const double* gU_out, const double* gphi_out, double* gU_in, double* gphi_in);
+
+/* Objective of the differentiation workload: J = sum over the outer radial faces of
+ * phi_f^2 / A_f (the integral of the face-mean B_r^2 over r_out).  phi_dev: device
+ * double[F]; J: host scalar; gphi_dev: device double[F] receiving dJ/dphi, or NULL.
+ * Synchronises the stream. */
+int geo_outer_Br2(geo_mesh_t mesh, const double* phi_dev, double* J, double* gphi_dev);
 
 /* Per-stage device timing, accumulated with CUDA events on the mesh stream while
  * enabled.  ms and counts: arrays of GEO_N_STAGES entries in the order

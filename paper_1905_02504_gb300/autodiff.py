@@ -1,0 +1,64 @@
+"""torch.autograd wrappers of the step and of the outer-shell objective.
+
+StepWindow runs K steps of fixed dt through the C ABI, keeping one checkpoint
+(U, phi) per step on the device; its backward walks the steps in reverse and
+calls geo_step_adjoint on each checkpoint (the step is recomputed inside the
+adjoint call).  OuterBr2 is J = sum over the outer radial faces of phi^2 / A.
+Both compute only in the CUDA library; torch provides the tensors.
+"""
+import torch
+
+from . import geomhd
+
+
+class StepWindow(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, phi, mesh, dt, K):
+        U = U.detach().contiguous()
+        phi = phi.detach().contiguous()
+        checkpoints = []
+        geomhd.geo_state_upload(mesh.h, U, phi)
+        cur_U, cur_phi = U, phi
+        for _ in range(K):
+            checkpoints.append((cur_U, cur_phi))
+            geomhd.geo_step(mesh.h, dt)
+            cur_U = torch.empty_like(U)
+            cur_phi = torch.empty_like(phi)
+            geomhd.geo_state_download(mesh.h, cur_U, cur_phi)
+        ctx.mesh, ctx.dt, ctx.checkpoints = mesh, dt, checkpoints
+        return cur_U, cur_phi
+
+    @staticmethod
+    def backward(ctx, gU, gphi):
+        gU = (torch.zeros_like(ctx.checkpoints[0][0]) if gU is None else gU).contiguous()
+        gphi = (torch.zeros_like(ctx.checkpoints[0][1]) if gphi is None else gphi).contiguous()
+        for U_s, phi_s in reversed(ctx.checkpoints):
+            gU_in = torch.empty_like(gU)
+            gphi_in = torch.empty_like(gphi)
+            geomhd.geo_step_adjoint(ctx.mesh.h, ctx.dt, U_s, phi_s, gU, gphi, gU_in, gphi_in)
+            gU, gphi = gU_in, gphi_in
+        torch.cuda.current_stream().synchronize()
+        return gU, gphi, None, None, None
+
+
+class OuterBr2(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phi, mesh):
+        phi = phi.detach().contiguous()
+        g = torch.empty_like(phi)
+        J = geomhd.geo_outer_Br2(mesh.h, phi, g)
+        ctx.save_for_backward(g)
+        return torch.tensor(J, dtype=phi.dtype, device=phi.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return g * gJ, None
+
+
+def step_window(mesh, U, phi, dt, K):
+    return StepWindow.apply(U, phi, mesh, dt, K)
+
+
+def outer_br2(mesh, phi):
+    return OuterBr2.apply(phi, mesh)

@@ -42,6 +42,11 @@ struct geo_mesh {
   std::vector<void*> allocs;
   bool timing = false;
   std::vector<PendingTiming> pending;
+  // adjoint work buffers (allocated on the first geo_step_adjoint call)
+  bool adj_ready = false;
+  geo::DevState adj_fwd{};
+  geo::AdjState adj{};
+  double* adj_U0 = nullptr;
   double ms[geo::N_STAGES] = {};
   int64_t cnt[geo::N_STAGES] = {};
 
@@ -156,6 +161,8 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.F_rad = T.F_rad;
   D.E_rad = T.E_rad;
   D.gamma = 5.0 / 3.0;
+  D.positivity = 0;
+  D.predictor = (prec == GEO_FP32_BULK) ? GEO_PRED_NODE_TEAM : GEO_PRED_ZONE_THREAD;
   std::vector<double> qpow(T.nr + 2);
   for (int k = 0; k < T.nr + 2; ++k) qpow[k] = std::pow(T.q, k);
   D.qpow = m->upload(qpow, err);
@@ -179,8 +186,18 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.nF = m->upload(T.nF, err);
   D.wF = m->upload(T.wF, err);
   D.WF = m->upload(T.WF, err);
-  D.GB = m->upload(T.GB, err);
-  D.TN = m->upload(T.TN, err);
+  // GB and TN transposed per column (team threads read consecutive rows)
+  const int NR = 3 + 3 * d.N;
+  std::vector<double> GBt(T.GB.size()), TNt(T.TN.size());
+  for (int c = 0; c < T.ncol; ++c) {
+    const size_t g0 = static_cast<size_t>(c) * NR * d.NBIN, t0 = static_cast<size_t>(c) * d.N * d.NC1;
+    for (int r = 0; r < NR; ++r)
+      for (int b = 0; b < d.NBIN; ++b) GBt[g0 + static_cast<size_t>(b) * NR + r] = T.GB[g0 + static_cast<size_t>(r) * d.NBIN + b];
+    for (int i = 0; i < d.N; ++i)
+      for (int mm = 0; mm < d.NC1; ++mm) TNt[t0 + static_cast<size_t>(mm) * d.N + i] = T.TN[t0 + static_cast<size_t>(i) * d.NC1 + mm];
+  }
+  D.GB = m->upload(GBt, err);
+  D.TN = m->upload(TNt, err);
   D.J0 = m->upload(T.J0, err);
   D.iJ0 = m->upload(T.iJ0, err);
   D.Sm = m->upload(T.Sm, err);
@@ -205,6 +222,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.sv_le = m->upload(T.sv_le, err);
   D.sv_fL = m->upload(T.sv_fL, err);
   D.sv_fR = m->upload(T.sv_fR, err);
+  D.sv_fse = m->upload(T.sv_fse, err);
   D.sv_fn = m->upload(T.sv_fn, err);
   D.sv_t = m->upload(T.sv_t, err);
   D.sv_dlw = m->upload(T.sv_dlw, err);
@@ -220,8 +238,8 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
     b.TF = m->upload_f32(T.TF, err);
     b.nF = m->upload_f32(T.nF, err);
     b.wF = m->upload_f32(T.wF, err);
-    b.GB = m->upload_f32(T.GB, err);
-    b.TN = m->upload_f32(T.TN, err);
+    b.GB = m->upload_f32(GBt, err);
+    b.TN = m->upload_f32(TNt, err);
     b.J0 = m->upload_f32(T.J0, err);
     b.iJ0 = m->upload_f32(T.iJ0, err);
     b.Sm = m->upload_f32(T.Sm, err);
@@ -278,6 +296,20 @@ int geo_mesh_sizes(geo_mesh_t m, int64_t* nz, int64_t* nf, int64_t* ne) {
 int geo_set_gamma(geo_mesh_t m, double gamma) {
   if (!m || !(gamma > 1.0)) return fail(GEO_ERR_ARG, "need a mesh and gamma > 1");
   m->dt.gamma = gamma;
+  return GEO_OK;
+}
+
+int geo_set_positivity(geo_mesh_t m, int enable) {
+  if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
+  m->dt.positivity = enable ? 1 : 0;
+  return GEO_OK;
+}
+
+int geo_set_predictor(geo_mesh_t m, int schedule) {
+  if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
+  if (schedule != GEO_PRED_ZONE_THREAD && schedule != GEO_PRED_NODE_TEAM)
+    return fail(GEO_ERR_ARG, "unknown predictor schedule");
+  m->dt.predictor = schedule;
   return GEO_OK;
 }
 
@@ -453,6 +485,86 @@ int geo_debug_buffer(geo_mesh_t m, int which, double* host, int64_t count) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "debug copy");
+  return GEO_OK;
+}
+
+static int ensure_adjoint_buffers(geo_mesh* m) {
+  if (m->adj_ready) return GEO_OK;
+  const geo::Dims& d = m->T.d;
+  const size_t Z = m->T.Z, F = m->T.F, E = m->T.E;
+  const int nqmax = d.NQR > d.NQS ? d.NQR : d.NQS;
+  cudaError_t err = cudaSuccess;
+  geo::DevState& S = m->adj_fwd;
+  S.U = m->alloc(8 * Z, err);
+  S.phi = m->alloc(F, err);
+  S.Wc = m->alloc(static_cast<size_t>(8) * d.NC1 * Z, err);
+  S.Bp = m->alloc(static_cast<size_t>(nqmax) * F, err);
+  S.trF = m->alloc(static_cast<size_t>(d.M - 1) * d.NQT * 8 * Z, err);
+  S.trE = m->alloc(static_cast<size_t>(d.M - 1) * 12 * d.NS * 8 * Z, err);
+  S.Ff = m->alloc(8 * F, err);
+  S.Ee = m->alloc(E, err);
+  S.red = m->ds.red;
+  m->adj_U0 = m->alloc(8 * Z, err);
+  geo::AdjState& A = m->adj;
+  A.gFf = m->alloc(8 * F, err);
+  A.gEe = m->alloc(E, err);
+  A.gtrF = m->alloc(static_cast<size_t>(d.M - 1) * d.NQT * 8 * Z, err);
+  A.gtrE = m->alloc(static_cast<size_t>(d.M - 1) * 12 * d.NS * 8 * Z, err);
+  A.gW = m->alloc(static_cast<size_t>(8) * d.NC1 * Z, err);
+  A.gBpz = m->alloc(static_cast<size_t>(d.NQT) * Z, err);
+  A.gphiz = m->alloc(6 * Z, err);
+  A.U0 = m->adj_U0;
+  if (err != cudaSuccess) return cuda_fail(err, "adjoint buffers");
+  m->adj_ready = true;
+  return GEO_OK;
+}
+
+int geo_step_adjoint(geo_mesh_t m, double dt, const double* U_in, const double* phi_in, const double* gU_out,
+                     const double* gphi_out, double* gU_in, double* gphi_in) {
+  if (!m || !U_in || !phi_in || !gU_out || !gphi_out || !gU_in || !gphi_in || !(dt > 0.0))
+    return fail(GEO_ERR_ARG, "geo_step_adjoint: bad arguments");
+  if (m->prec != GEO_FP64) return fail(GEO_ERR_ARG, "geo_step_adjoint: the adjoint is available for GEO_FP64 meshes");
+  int rc = ensure_adjoint_buffers(m);
+  if (rc != GEO_OK) return rc;
+  const size_t Z = m->T.Z, F = m->T.F;
+  cudaError_t e = cudaMemcpyAsync(m->adj_U0, U_in, 8 * Z * sizeof(double), cudaMemcpyDeviceToDevice, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_fwd.U, U_in, 8 * Z * sizeof(double), cudaMemcpyDeviceToDevice, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_fwd.phi, phi_in, F * sizeof(double), cudaMemcpyDeviceToDevice, m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint checkpoint copy");
+  // forward intermediates of the checkpoint state
+  for (int s = geo::ST_WENO; s <= geo::ST_ADER && e == cudaSuccess; ++s) {
+    switch (m->order) {
+      case 2: e = geo::launch_stage<2, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
+      case 3: e = geo::launch_stage<3, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
+      default: e = geo::launch_stage<4, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint forward recompute");
+  geo::AdjState A = m->adj;
+  A.gUp = gU_out;
+  A.gphip = gphi_out;
+  A.gU = gU_in;
+  A.gphi = gphi_in;
+  // the forward k_ader overwrote the zone B of the working copy; the adjoint
+  // kernels read the pristine checkpoint (A.U0) and the pre-step face fluxes
+  geo::DevState S = m->adj_fwd;
+  switch (m->order) {
+    case 2: e = geo::launch_adjoint<2>(m->dt, S, A, dt, m->st); break;
+    case 3: e = geo::launch_adjoint<3>(m->dt, S, A, dt, m->st); break;
+    default: e = geo::launch_adjoint<4>(m->dt, S, A, dt, m->st); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  return GEO_OK;
+}
+
+int geo_outer_Br2(geo_mesh_t m, const double* phi_dev, double* J, double* gphi_dev) {
+  if (!m || !phi_dev || !J) return fail(GEO_ERR_ARG, "geo_outer_Br2: bad arguments");
+  cudaError_t e = cudaSuccess;
+  if (gphi_dev) e = cudaMemsetAsync(gphi_dev, 0, m->T.F * sizeof(double), m->st);
+  if (e == cudaSuccess) e = geo::launch_outer_br2(m->dt, phi_dev, m->ds.red + 3000, gphi_dev, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(J, m->ds.red + 3000, sizeof(double), cudaMemcpyDeviceToHost, m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "geo_outer_Br2");
   return GEO_OK;
 }
 

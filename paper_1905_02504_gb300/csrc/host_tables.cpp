@@ -918,6 +918,7 @@ struct Builder {
         }
         T.sv_fL[4 * v + j] = iL;
         T.sv_fR[4 * v + j] = iR;
+        T.sv_fse[4 * v + j] = e;
         vector<V3> X = zone_nodes(cL, 0);
         int le = T.sv_le[4 * v + iL];
         int lfL = T.se_lf[2 * e];
@@ -1161,6 +1162,7 @@ struct Builder {
     T.sv_le.assign(4 * T.nsv, 0);
     T.sv_fL.assign(4 * T.nsv, 0);
     T.sv_fR.assign(4 * T.nsv, 0);
+    T.sv_fse.assign(4 * T.nsv, 0);
     T.sv_fn.assign(static_cast<size_t>(T.nsv) * 4 * NS * 3, 0.0);
     T.sv_dlw.assign(static_cast<size_t>(T.nsv) * NS, 0.0);
     sphere_vertex_tables();

@@ -98,6 +98,7 @@ struct Tables {
   std::vector<int> sv_col;     // [nsv][4]
   std::vector<int> sv_le;      // [nsv][4]
   std::vector<int> sv_fL, sv_fR;  // [nsv][4]
+  std::vector<int> sv_fse;     // [nsv][4]   sphere edge of face j (faces (se, k) around the edge)
   std::vector<double> sv_fn;   // [nsv][4][NS][3]
   std::vector<double> sv_t;    // [nsv][3]
   std::vector<double> sv_dlw;  // [nsv][NS] at shell 0

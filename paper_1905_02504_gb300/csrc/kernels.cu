@@ -12,6 +12,7 @@
 // updates of U and Phi are FP64 in both forms, so div B stays at FP64 rounding.
 #include "device.cuh"
 #include "host_tables.h"
+#include "mhd_device.cuh"
 
 #include <cfloat>
 
@@ -40,156 +41,7 @@ GEO_RC(4, float, c_ref4f)
 
 namespace {
 
-constexpr int TPB = 128;
-
-template <typename R> __device__ __forceinline__ const BulkTables<R>& bulk(const DevTables& T);
-template <> __device__ __forceinline__ const BulkTables<double>& bulk<double>(const DevTables& T) { return T.b64; }
-template <> __device__ __forceinline__ const BulkTables<float>& bulk<float>(const DevTables& T) { return T.b32; }
-
-// ----------------------------------------------------------------------------
-// ideal MHD (Eq. 2.2 in rationalised units), in the bulk type R
-// ----------------------------------------------------------------------------
-template <typename R>
-struct Prim {
-  R rho, vx, vy, vz, p, bx, by, bz;
-};
-
-template <typename R>
-__device__ __forceinline__ Prim<R> to_prim(const R* u, R g) {
-  Prim<R> w;
-  w.rho = u[0];
-  R ir = R(1) / u[0];
-  w.vx = u[1] * ir;
-  w.vy = u[2] * ir;
-  w.vz = u[3] * ir;
-  w.bx = u[5];
-  w.by = u[6];
-  w.bz = u[7];
-  w.p = (g - R(1)) * (u[4] - R(0.5) * w.rho * (w.vx * w.vx + w.vy * w.vy + w.vz * w.vz) -
-                      R(0.5) * (w.bx * w.bx + w.by * w.by + w.bz * w.bz));
-  return w;
-}
-
-// F(U).n for any vector n
-template <typename R>
-__device__ __forceinline__ void flux_n(const R* u, const Prim<R>& w, R nx, R ny, R nz, R* F) {
-  R vn = w.vx * nx + w.vy * ny + w.vz * nz;
-  R bn = w.bx * nx + w.by * ny + w.bz * nz;
-  R pt = w.p + R(0.5) * (w.bx * w.bx + w.by * w.by + w.bz * w.bz);
-  R vb = w.vx * w.bx + w.vy * w.by + w.vz * w.bz;
-  F[0] = w.rho * vn;
-  F[1] = u[1] * vn + pt * nx - w.bx * bn;
-  F[2] = u[2] * vn + pt * ny - w.by * bn;
-  F[3] = u[3] * vn + pt * nz - w.bz * bn;
-  F[4] = (u[4] + pt) * vn - bn * vb;
-  F[5] = w.bx * vn - w.vx * bn;
-  F[6] = w.by * vn - w.vy * bn;
-  F[7] = w.bz * vn - w.vz * bn;
-}
-
-template <typename R>
-__device__ __forceinline__ R fast_speed(const Prim<R>& w, R nx, R ny, R nz, R g) {
-  R ir = R(1) / w.rho;
-  R a2 = g * w.p * ir;
-  R b2 = (w.bx * w.bx + w.by * w.by + w.bz * w.bz) * ir;
-  R bn = w.bx * nx + w.by * ny + w.bz * nz;
-  R bn2 = bn * bn * ir;
-  R s = a2 + b2;
-  return sqrt(R(0.5) * (s + sqrt(fmax(s * s - R(4) * a2 * bn2, R(0)))));
-}
-
-// HLL flux along the unit normal (Davis wave speeds); the weighted flux is
-// accumulated in FP64
-template <typename R>
-__device__ __forceinline__ void hll_acc(const R* uL, const R* uR, R nx, R ny, R nz, R g, double w,
-                                        double* acc) {
-  Prim<R> a = to_prim(uL, g), b = to_prim(uR, g);
-  R vnL = a.vx * nx + a.vy * ny + a.vz * nz;
-  R vnR = b.vx * nx + b.vy * ny + b.vz * nz;
-  R cL = fast_speed(a, nx, ny, nz, g), cR = fast_speed(b, nx, ny, nz, g);
-  R SL = fmin(vnL - cL, vnR - cR);
-  R SR = fmax(vnL + cL, vnR + cR);
-  R FL[8], FR[8];
-  flux_n(uL, a, nx, ny, nz, FL);
-  flux_n(uR, b, nx, ny, nz, FR);
-  if (SL >= R(0)) {
-#pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FL[v]);
-  } else if (SR <= R(0)) {
-#pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FR[v]);
-  } else {
-    R id = R(1) / (SR - SL);
-#pragma unroll
-    for (int v = 0; v < 8; ++v)
-      acc[v] += w * static_cast<double>((SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * id);
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ R rusanov_speed(const R* u, R nx, R ny, R nz, R g) {
-  Prim<R> w = to_prim(u, g);
-  return fabs(w.vx * nx + w.vy * ny + w.vz * nz) + fast_speed(w, nx, ny, nz, g);
-}
-
-template <typename R>
-__device__ __forceinline__ R minmod(R a, R b) {
-  if (a * b > R(0)) return (a > R(0) ? R(1) : R(-1)) * fmin(fabs(a), fabs(b));
-  return R(0);
-}
-
-__device__ __forceinline__ int side_of_lf(int lf) { return lf == 0 ? 3 : (lf == 1 ? 1 : (lf == 2 ? 0 : 2)); }
-
-template <int P>
-__device__ __forceinline__ int foff(int lf) {
-  using Dm = Dim<P>;
-  return lf < 4 ? lf * Dm::NQS : 4 * Dm::NQS + (lf - 4) * Dm::NQR;
-}
-template <int P>
-__device__ __forceinline__ int nq_of(int lf) {
-  return lf < 4 ? Dim<P>::NQS : Dim<P>::NQR;
-}
-
-// face f -> L zone / local face, R zone / local face (-1 when on the boundary),
-// the column and local face whose tables hold the face geometry, shell index k
-struct FaceInfo {
-  long long zL, zR;
-  int lfL, lfR, cg, lfg, k, se;
-  double gsign;  // canonical normal = gsign * outward normal of (cg, lfg)
-};
-
-__device__ __forceinline__ FaceInfo face_info(const DevTables& T, long long f) {
-  FaceInfo fi;
-  int nr = T.nr;
-  if (f < T.F_rad) {
-    int c = static_cast<int>(f / (nr + 1));
-    int k = static_cast<int>(f % (nr + 1));
-    fi.zL = (k >= 1) ? static_cast<long long>(c) * nr + k - 1 : -1;
-    fi.zR = (k < nr) ? static_cast<long long>(c) * nr + k : -1;
-    fi.lfL = 5;
-    fi.lfR = 4;
-    fi.cg = c;
-    fi.lfg = 4;
-    fi.gsign = -1.0;
-    fi.k = k;
-    fi.se = -1;
-  } else {
-    long long r = f - T.F_rad;
-    int se = static_cast<int>(r / nr);
-    int k = static_cast<int>(r % nr);
-    int cL = T.se_col[2 * se], cR = T.se_col[2 * se + 1];
-    fi.zL = static_cast<long long>(cL) * nr + k;
-    fi.zR = static_cast<long long>(cR) * nr + k;
-    fi.lfL = T.se_lf[2 * se];
-    fi.lfR = T.se_lf[2 * se + 1];
-    fi.cg = cL;
-    fi.lfg = fi.lfL;
-    fi.gsign = 1.0;
-    fi.k = k;
-    fi.se = se;
-  }
-  return fi;
-}
+using namespace dev;
 
 // ----------------------------------------------------------------------------
 // a1: WENO-AO reconstruction (Sec. III)
@@ -386,7 +238,9 @@ __device__ void flux_difference(const DevTables& T, int c, const R (*Uh)[8], R (
   }
 }
 
-template <int P, typename R>
+// POS: the positivity scaling of the nodal states (Sec. VI step 3) is compiled in only
+// when the switch is on, so the plain predictor keeps its register budget
+template <int P, typename R, bool POS>
 __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restrict__ U,
                                               const double* __restrict__ phi, const R* __restrict__ Wc,
                                               const R* __restrict__ Bp, R* __restrict__ trF,
@@ -441,7 +295,7 @@ __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restr
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R s = R(0);
-    for (int b = 0; b < NBIN; ++b) s += GB[d * NBIN + b] * in[b];
+    for (int b = 0; b < NBIN; ++b) s += GB[b * (3 + 3 * N) + d] * in[b];
     Uz[5 + d] = s;
     U[(5 + d) * Z + z] = static_cast<double>(s);  // Sec. IV.b step 10: zone B <- divergence-free mean
   }
@@ -455,18 +309,36 @@ __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restr
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R s = Uz[v];
-      for (int m = 0; m < NC1; ++m) s += TN[i * NC1 + m] * Wc[(v * NC1 + m) * Z + z];
+      for (int m = 0; m < NC1; ++m) s += TN[m * N + i] * Wc[(v * NC1 + m) * Z + z];
       u[v] = s;
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const R* row = GB + (3 + d * N + i) * NBIN;
       R s = R(0);
-      for (int b = 0; b < NBIN; ++b) s += row[b] * in[b];
+      for (int b = 0; b < NBIN; ++b) s += GB[b * (3 + 3 * N) + 3 + d * N + i] * in[b];
       u[5 + d] = s;
     }
+    const R jf = POS ? R(1) : J0[i];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) Uh[0][i][v] = J0[i] * u[v];
+    for (int v = 0; v < 8; ++v) Uh[0][i][v] = jf * u[v];
+  }
+  if constexpr (POS) {
+    const R gR = static_cast<R>(T.gamma);
+    const R pbar = pressure_of(Uz, gR);
+    const R eps_r = fmin(R(1e-13), Uz[0]), eps_p = fmin(R(1e-13), pbar);
+    R th_r = R(1), th_p = R(1);
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) pos_rho(Uh[0][i], Uz, eps_r, th_r);
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) pos_p(Uh[0][i], Uz, th_r, gR, pbar, eps_p, th_p);
+    const R th = th_r * th_p;
+#pragma unroll 1
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const R uv = th < R(1) ? Uz[v] + th * (Uh[0][i][v] - Uz[v]) : Uh[0][i][v];
+        Uh[0][i][v] = J0[i] * uv;
+      }
   }
 #pragma unroll 1
   for (int m = 1; m < M; ++m)
@@ -481,8 +353,19 @@ __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restr
   flux_difference<P, R>(T, c, Uh[0], dF1);
 #pragma unroll 1
   for (int it = 0; it < P; ++it) {
+    // in the first iteration every level still equals level 1, so its flux
+    // difference is dF1 bit for bit
 #pragma unroll 1
-    for (int m = 1; m < M; ++m) flux_difference<P, R>(T, c, Uh[m], dFm[m - 1]);
+    for (int m = 1; m < M; ++m) {
+      if (it == 0) {
+#pragma unroll 1
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) dFm[m - 1][i][v] = dF1[i][v];
+      } else {
+        flux_difference<P, R>(T, c, Uh[m], dFm[m - 1]);
+      }
+    }
 #pragma unroll 1
     for (int kk = 1; kk < M; ++kk) {
       R rk[M];
@@ -551,6 +434,394 @@ __global__ void __launch_bounds__(TPB) k_ader(const DevTables T, double* __restr
       }
 }
 
+// Positivity scaling of the predicted face and edge point states (Sec. VI step 3):
+// one theta per zone over all its traces at all Gauss times, about the zone mean
+// (whose B the predictor has just replaced by the divergence-free mean).
+template <int P, typename R>
+__global__ void __launch_bounds__(TPB) k_pos_traces(const DevTables T, const double* __restrict__ U,
+                                                    R* __restrict__ trF, R* __restrict__ trE) {
+  using Dm = Dim<P>;
+  constexpr int M = Dm::M, NQT = Dm::NQT, NS = Dm::NS;
+  constexpr int NPF = (M - 1) * NQT, NPE = (M - 1) * 12 * NS;
+  long long z = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (z >= T.Z) return;
+  const long long Z = T.Z;
+  R Uz[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) Uz[v] = static_cast<R>(U[v * Z + z]);
+  const R gR = static_cast<R>(T.gamma);
+  const R pbar = pressure_of(Uz, gR);
+  const R eps_r = fmin(R(1e-13), Uz[0]), eps_p = fmin(R(1e-13), pbar);
+  R th_r = R(1), th_p = R(1);
+  for (int pass = 0; pass < 3; ++pass) {
+    const R th = th_r * th_p;
+    if (pass == 2 && !(th < R(1))) break;
+#pragma unroll 1
+    for (int t = 0; t < NPF + NPE; ++t) {
+      R* base = (t < NPF) ? trF + (static_cast<size_t>(t) * 8) * Z + z
+                          : trE + (static_cast<size_t>(t - NPF) * 8) * Z + z;
+      R s[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) s[v] = base[v * Z];
+      if (pass == 0) pos_rho(s, Uz, eps_r, th_r);
+      else if (pass == 1) pos_p(s, Uz, th_r, gR, pbar, eps_p, th_p);
+      else
+#pragma unroll
+        for (int v = 0; v < 8; ++v) base[v * Z] = Uz[v] + th * (s[v] - Uz[v]);
+    }
+  }
+}
+
+
+// ----------------------------------------------------------------------------
+// a2 (zone part) + a3 with one thread per serendipity node: a team of N threads
+// per zone, ZB zones per block.  Node i's M time levels and flux differences
+// live in its thread's registers; at each flux evaluation the team exchanges
+// the three metric fluxes of its nodes through shared memory and each thread
+// gathers its own row of D^alpha (row form, RL entries).  Point values at the
+// zone's face and edge points are then formed from the final levels in shared
+// memory by threads mapped zone-fastest, so that the SoA trace writes of the ZB
+// zones of a block are contiguous.
+// ----------------------------------------------------------------------------
+template <int P> struct Team;
+template <> struct Team<2> { static constexpr int ZB = 16; };
+template <> struct Team<3> { static constexpr int ZB = 8; };
+template <> struct Team<4> { static constexpr int ZB = 4; };
+
+template <int P, typename R>
+struct TeamSmem {
+  using Dm = Dim<P>;
+  static constexpr int ZB = Team<P>::ZB;
+  alignas(16) R X[ZB][3][Dm::N][8];  // fluxes of one level / the final levels
+  R in[ZB][Dm::NBIN];                // inputs of the divergence-free reconstruction
+  R W[ZB][5 * Dm::NC1];              // fluid Taylor coefficients
+  R Uz[ZB][8];                       // zone means (B: the divergence-free mean)
+  R Ev[3 * Dm::RL * Dm::N];
+  R psiF[Dm::NQT * Dm::NFN];
+  R psiE[12 * Dm::NS * Dm::NEN];
+  R th[ZB][4];                       // positivity factors (min-reduced)
+  unsigned char Ec[3 * Dm::RL * Dm::N];
+  unsigned char fnode[6 * Dm::NFN];
+  unsigned char enode[12 * Dm::NEN];
+};
+
+// min-reduction of a non-negative factor in shared memory (the bit patterns of
+// non-negative IEEE numbers order like the numbers)
+__device__ __forceinline__ void smem_min_nonneg(float* a, float v) {
+  atomicMin(reinterpret_cast<int*>(a), __float_as_int(v));
+}
+__device__ __forceinline__ void smem_min_nonneg(double* a, double v) {
+  atomicMin(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// one flux difference of node i of a team: dF = sum_alpha sum_j D^alpha_ij F^alpha_j - F_i . g_i
+template <int P, typename R>
+__device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, const R* g, const R* Sa, R gam,
+                                                     R (*X)[Dim<P>::N][8], const R* Ev, const unsigned char* Ec,
+                                                     int i, bool valid) {
+  using Dm = Dim<P>;
+  constexpr int N = Dm::N, RL = Dm::RL;
+  if (valid) {
+    R u[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) u[v] = Uh[v] * iJ;
+    Prim<R> w = to_prim(u, gam);
+    R G[8];
+    flux_n(u, w, g[0], g[1], g[2], G);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) dF[v] = -G[v];
+#pragma unroll
+    for (int al = 0; al < 3; ++al) {
+      R Fa[8];
+      flux_n(u, w, Sa[3 * al], Sa[3 * al + 1], Sa[3 * al + 2], Fa);
+#pragma unroll
+      for (int v = 0; v < 8; ++v) X[al][i][v] = Fa[v];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int sl = 0; sl < RL; ++sl) {
+        const R d = Ev[(al * RL + sl) * N + i];
+        const R* Fj = X[al][Ec[(al * RL + sl) * N + i]];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) dF[v] += d * Fj[v];
+      }
+  }
+  __syncthreads();
+}
+
+template <int P, typename R, bool POS>
+__global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
+    k_ader_team(const DevTables T, double* __restrict__ U, const double* __restrict__ phi,
+                const R* __restrict__ Wc, const R* __restrict__ Bp, R* __restrict__ trF, R* __restrict__ trE,
+                double dt) {
+  using Dm = Dim<P>;
+  constexpr int N = Dm::N, M = Dm::M, NC1 = Dm::NC1, NC = Dm::NC, NQT = Dm::NQT, NS = Dm::NS,
+                NBIN = Dm::NBIN, NR = 3 + 3 * Dm::N, ZB = Team<P>::ZB, NT = ZB * N;
+  __shared__ TeamSmem<P, R> S;
+  const RefConst<P, R>& K = RC<P, R>::get();
+  const BulkTables<R>& BT = bulk<R>(T);
+  const long long Z = T.Z, F = T.F;
+  const int nr = T.nr;
+  const int tid = threadIdx.x;
+  const long long zbase = static_cast<long long>(blockIdx.x) * ZB;
+  // ---- reference tables and zone inputs into shared memory
+  for (int t = tid; t < 3 * Dm::RL * N; t += NT) {
+    S.Ev[t] = K.Eval[t];
+    S.Ec[t] = K.Ecol[t];
+  }
+  for (int t = tid; t < NQT * Dm::NFN; t += NT) S.psiF[t] = K.psiFc[t];
+  for (int t = tid; t < 6 * Dm::NFN; t += NT) S.fnode[t] = K.fnode[t];
+  for (int t = tid; t < 12 * NS * Dm::NEN; t += NT) S.psiE[t] = K.psiEc[t];
+  for (int t = tid; t < 12 * Dm::NEN; t += NT) S.enode[t] = K.enode[t];
+  for (int w = tid; w < ZB * 4; w += NT) S.th[w / 4][w % 4] = R(1);
+  for (int w = tid; w < ZB * 3 * NC; w += NT) {
+    const int zl = w % ZB, e = w / ZB, d = e / NC, t = e % NC;
+    const long long z = zbase + zl;
+    if (z < Z) S.in[zl][e] = (t == 0) ? static_cast<R>(U[(5 + d) * Z + z]) : Wc[((5 + d) * NC1 + t - 1) * Z + z];
+  }
+  for (int w = tid; w < ZB * 5 * NC1; w += NT) {
+    const int zl = w % ZB, e = w / ZB;
+    const long long z = zbase + zl;
+    if (z < Z) S.W[zl][e] = Wc[static_cast<size_t>(e) * Z + z];
+  }
+  for (int w = tid; w < ZB * 5; w += NT) {
+    const int zl = w % ZB, v = w / ZB;
+    const long long z = zbase + zl;
+    if (z < Z) S.Uz[zl][v] = static_cast<R>(U[v * Z + z]);
+  }
+  for (int w = tid; w < ZB * 6; w += NT) {
+    const int zl = w % ZB, lf = w / ZB;
+    const long long z = zbase + zl;
+    if (z >= Z) continue;
+    const int c = static_cast<int>(z / nr), k = static_cast<int>(z % nr);
+    const double s1 = T.qpow[k];
+    long long f;
+    int sg, se = -1;
+    if (lf < 4) {
+      const int sd = side_of_lf(lf);
+      se = T.col_side_se[4 * c + sd];
+      sg = T.col_side_sgn[4 * c + sd];
+      f = T.F_rad + static_cast<long long>(se) * nr + k;
+    } else {
+      f = static_cast<long long>(c) * (nr + 1) + k + (lf == 5 ? 1 : 0);
+      sg = lf == 5 ? 1 : -1;
+    }
+    const R rsg = static_cast<R>(sg);
+    const int nq = nq_of<P>(lf);
+    for (int q = 0; q < nq; ++q) {
+      const int ql = (lf < 4 && sg < 0) ? T.se_perm[se * Dm::NQS + q] : q;
+      S.in[zl][3 * NC + foff<P>(lf) + ql] = rsg * Bp[static_cast<size_t>(q) * F + f];
+    }
+    const double s2 = s1 * s1;
+    S.in[zl][3 * NC + NQT + lf] = static_cast<R>(sg * phi[f] / (T.A0[6 * c + lf] * s2));
+  }
+  __syncthreads();
+  // ---- zone-mean B (Sec. IV.b step 10)
+  if (tid < 3 * ZB) {
+    const int zl = tid % ZB, d = tid / ZB;
+    const long long z = zbase + zl;
+    if (z < Z) {
+      const int c = static_cast<int>(z / nr);
+      const R* GB = BT.GB + static_cast<size_t>(c) * NR * NBIN;
+      R s = R(0);
+      for (int b = 0; b < NBIN; ++b) s += GB[b * NR + d] * S.in[zl][b];
+      S.Uz[zl][5 + d] = s;
+      U[(5 + d) * Z + z] = static_cast<double>(s);
+    }
+  }
+  __syncthreads();
+  // ---- node of this thread
+  const int zl = tid / N, i = tid % N;
+  const long long z = zbase + zl;
+  const bool valid = z < Z;
+  const int c = valid ? static_cast<int>(z / nr) : 0;
+  const int k = valid ? static_cast<int>(z % nr) : 0;
+  const R gam = static_cast<R>(T.gamma);
+  R Uh[M][8];
+  {
+    R u[8];
+    if (valid) {
+      const R* TN = BT.TN + static_cast<size_t>(c) * N * NC1;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        R s = S.Uz[zl][v];
+        for (int m = 0; m < NC1; ++m) s += TN[m * N + i] * S.W[zl][v * NC1 + m];
+        u[v] = s;
+      }
+      const R* GB = BT.GB + static_cast<size_t>(c) * NR * NBIN;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        R s = R(0);
+        for (int b = 0; b < NBIN; ++b) s += GB[b * NR + 3 + d * N + i] * S.in[zl][b];
+        u[5 + d] = s;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 8; ++v) u[v] = R(1);
+    }
+    if constexpr (POS) {
+      const R* Uz = S.Uz[zl];
+      const R pbar = pressure_of(Uz, gam);
+      const R eps_r = fmin(R(1e-13), Uz[0]), eps_p = fmin(R(1e-13), pbar);
+      R th_r = R(1), th_p = R(1);
+      pos_rho(u, Uz, eps_r, th_r);
+      if (valid && th_r < R(1)) smem_min_nonneg(&S.th[zl][0], th_r);
+      __syncthreads();
+      th_r = S.th[zl][0];
+      pos_p(u, Uz, th_r, gam, pbar, eps_p, th_p);
+      if (valid && th_p < R(1)) smem_min_nonneg(&S.th[zl][1], th_p);
+      __syncthreads();
+      const R th = th_r * S.th[zl][1];
+      if (th < R(1)) {
+#pragma unroll
+        for (int v = 0; v < 8; ++v) u[v] = Uz[v] + th * (u[v] - Uz[v]);
+      }
+    }
+    const R j0 = valid ? BT.J0[static_cast<size_t>(c) * N + i] : R(1);
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) Uh[m][v] = j0 * u[v];
+  }
+  // ---- metric terms of the node, kept for all flux evaluations
+  R iJ = R(1), g[3] = {R(0), R(0), R(0)}, Sa[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) Sa[t] = R(0);
+  if (valid) {
+    iJ = BT.iJ0[static_cast<size_t>(c) * N + i];
+    const R* gc = BT.gcl + (static_cast<size_t>(c) * N + i) * 3;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) g[t] = gc[t];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) Sa[3 * al + t] = BT.Sm[static_cast<size_t>(c) * 9 * N + (al * N + i) * 3 + t];
+  }
+  // ---- Picard iterations (Eqs. C.34-C.36); in the first iteration every level
+  // equals level 1, so its flux difference is reused
+  const R fs = static_cast<R>(dt / T.qpow[k]);
+  R (*X)[N][8] = S.X[zl];
+  R dF[M][8];
+  team_flux_difference<P, R>(Uh[0], dF[0], iJ, g, Sa, gam, X, S.Ev, S.Ec, i, valid);
+#pragma unroll
+  for (int m = 1; m < M; ++m)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) dF[m][v] = dF[0][v];
+#pragma unroll 1
+  for (int it = 0; it < P; ++it) {
+    if (it > 0) {
+#pragma unroll
+      for (int m = 1; m < M; ++m) team_flux_difference<P, R>(Uh[m], dF[m], iJ, g, Sa, gam, X, S.Ev, S.Ec, i, valid);
+    }
+#pragma unroll
+    for (int kk = 1; kk < M; ++kk) {
+      R rk[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) rk[m] = fs * K.R_[kk * M + m];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        R s = Uh[0][v] - rk[0] * dF[0][v];
+#pragma unroll
+        for (int m = 1; m < M; ++m) s -= rk[m] * dF[m][v];
+        Uh[kk][v] = s;
+      }
+    }
+  }
+  // ---- final levels to shared memory (the exchange buffer is free after the
+  // last flux difference's closing barrier)
+#pragma unroll
+  for (int m = 1; m < M; ++m)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) X[m - 1][i][v] = Uh[m][v];
+  __syncthreads();
+  // ---- point values; thread -> (zone zl2 = tid % ZB, point slots tid / ZB + N s)
+  {
+    constexpr int NPF = (M - 1) * NQT, NPE = (M - 1) * 12 * NS, NPT = NPF + NPE;
+    const int zl2 = tid % ZB;
+    const long long z2 = zbase + zl2;
+    const bool valid2 = z2 < Z;
+    const int c2 = valid2 ? static_cast<int>(z2 / nr) : 0;
+    const R* JF = BT.JF + static_cast<size_t>(c2) * NQT;
+    const R* JE = BT.JE + static_cast<size_t>(c2) * 12 * NS;
+    const R(*X2)[N][8] = S.X[zl2];
+    const R* Uz = S.Uz[zl2];
+    constexpr int NPASS = POS ? 3 : 1;
+    R pbar = R(0), eps_r = R(0), eps_p = R(0), th = R(1);
+    if constexpr (POS) {
+      pbar = pressure_of(Uz, gam);
+      eps_r = fmin(R(1e-13), Uz[0]);
+      eps_p = fmin(R(1e-13), pbar);
+    }
+#pragma unroll 1
+    for (int pass = 0; pass < NPASS; ++pass) {
+      if constexpr (POS) {
+        if (pass == 2) th = S.th[zl2][2] * S.th[zl2][3];
+      }
+#pragma unroll 1
+      for (int t = tid / ZB; t < NPT; t += N) {
+        R s[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) s[v] = R(0);
+        R* out;
+        if (t < NPF) {
+          const int m = t / NQT, idx = t % NQT;
+          const int lf = idx < 4 * Dm::NQS ? idx / Dm::NQS : 4 + (idx - 4 * Dm::NQS) / Dm::NQR;
+#pragma unroll
+          for (int a = 0; a < Dm::NFN; ++a) {
+            const R w = S.psiF[idx * Dm::NFN + a];
+            const R* x = X2[m][S.fnode[lf * Dm::NFN + a]];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) s[v] += w * x[v];
+          }
+          const R ij = valid2 ? R(1) / JF[idx] : R(1);
+#pragma unroll
+          for (int v = 0; v < 8; ++v) s[v] *= ij;
+          out = trF + (static_cast<size_t>(t) * 8) * Z + z2;
+        } else {
+          const int tt = t - NPF, m = tt / (12 * NS), idx = tt % (12 * NS), le = idx / NS;
+#pragma unroll
+          for (int a = 0; a < Dm::NEN; ++a) {
+            const R w = S.psiE[idx * Dm::NEN + a];
+            const R* x = X2[m][S.enode[le * Dm::NEN + a]];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) s[v] += w * x[v];
+          }
+          const R ij = valid2 ? R(1) / JE[idx] : R(1);
+#pragma unroll
+          for (int v = 0; v < 8; ++v) s[v] *= ij;
+          out = trE + (static_cast<size_t>(tt) * 8) * Z + z2;
+        }
+        if (!valid2) continue;
+        if constexpr (POS) {
+          if (pass == 0) {
+            R th_r = R(1);
+            pos_rho(s, Uz, eps_r, th_r);
+            if (th_r < R(1)) smem_min_nonneg(&S.th[zl2][2], th_r);
+            continue;
+          }
+          if (pass == 1) {
+            R th_p = R(1);
+            pos_p(s, Uz, S.th[zl2][2], gam, pbar, eps_p, th_p);
+            if (th_p < R(1)) smem_min_nonneg(&S.th[zl2][3], th_p);
+            continue;
+          }
+          if (th < R(1)) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) s[v] = Uz[v] + th * (s[v] - Uz[v]);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) out[v * Z] = s[v];
+      }
+      if constexpr (POS) __syncthreads();
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------
 // a4: face fluxes (HLL at face points x Gauss times, FP64 accumulation)
 // ----------------------------------------------------------------------------
@@ -582,14 +853,14 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* _
       double W = wt * T.WF[static_cast<size_t>(fi.cg) * NQT + ig] * s2;
       R uL[8], uR[8];
       if (fi.zL >= 0) {
-        const R* src = trF + (static_cast<size_t>((m - 1) * NQT + foff<P>(fi.lfL) + q) * 8) * Z + fi.zL;
+        const R* src = trF + trF_at<P>(fi.zL, m, foff<P>(fi.lfL) + q, Z);
 #pragma unroll
         for (int v = 0; v < 8; ++v) uL[v] = src[v * Z];
       }
       if (fi.zR >= 0) {
         int ql = q;
         if (fi.se >= 0) ql = T.se_perm[fi.se * Dm::NQS + q];
-        const R* src = trF + (static_cast<size_t>((m - 1) * NQT + foff<P>(fi.lfR) + ql) * 8) * Z + fi.zR;
+        const R* src = trF + trF_at<P>(fi.zR, m, foff<P>(fi.lfR) + ql, Z);
 #pragma unroll
         for (int v = 0; v < 8; ++v) uR[v] = src[v * Z];
       }
@@ -685,7 +956,7 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
       R st[4][8];
       for (int j = 0; j < nz; ++j) {
         int sl = revs[j] ? NS - 1 - s : s;
-        const R* src = trE + (static_cast<size_t>((m - 1) * 12 * NS + les[j] * NS + sl) * 8) * Z + zs[j];
+        const R* src = trE + trE_at<P>(zs[j], m, les[j] * NS + sl, Z);
 #pragma unroll
         for (int v = 0; v < 8; ++v) st[j][v] = src[v * Z];
       }
@@ -915,6 +1186,33 @@ __global__ void k_fma_probe(T_* out, int iters, T_ a, T_ b) {
 
 inline unsigned grid_for(long long n) { return static_cast<unsigned>((n + TPB - 1) / TPB); }
 
+#include "adjoint_kernels.inc"
+
+// objective of the differentiation workload: J = sum over the outer radial faces of
+// Phi_f^2 / A_f (the integral of <B_r>^2 over r_out); one block, deterministic
+__global__ void __launch_bounds__(256) k_outer_br2(const DevTables T, const double* __restrict__ phi,
+                                                   double* __restrict__ out, double* __restrict__ gphi) {
+  __shared__ double sm[8];
+  double acc = 0.0;
+  const int nr = T.nr;
+  const double s2 = T.qpow[nr] * T.qpow[nr];
+  for (int c = threadIdx.x; c < T.ncol; c += blockDim.x) {
+    const long long f = static_cast<long long>(c) * (nr + 1) + nr;
+    const double A = T.A0[6 * c + 4] * s2;
+    acc += phi[f] * phi[f] / A;
+    if (gphi) gphi[f] = 2.0 * phi[f] / A;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sm[w];
+    out[0] = s;
+  }
+}
+
 }  // namespace
 
 int reduction_blocks(long long n) {
@@ -922,36 +1220,6 @@ int reduction_blocks(long long n) {
   if (b > 1024) b = 1024;
   if (b < 1) b = 1;
   return static_cast<int>(b);
-}
-
-template <int P>
-cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, double dt, cudaStream_t st) {
-  switch (stage) {
-    case ST_WENO:
-      k_weno<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.Wc);
-      break;
-    case ST_BPERP:
-      k_bperp<P><<<grid_for(T.F), TPB, 0, st>>>(T, S.U, S.phi, S.Wc, S.Bp);
-      break;
-    case ST_ADER:
-      k_ader<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.phi, S.Wc, S.Bp, S.trF, S.trE, dt);
-      break;
-    case ST_FACE:
-      k_face_flux<P><<<grid_for(T.F), TPB, 0, st>>>(T, S.trF, S.Ff, dt);
-      break;
-    case ST_EDGE:
-      k_edge_emf<P><<<grid_for(T.E), TPB, 0, st>>>(T, S.trE, S.Ee, dt);
-      break;
-    case ST_UPD_U:
-      k_update_u<<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.Ff);
-      break;
-    case ST_UPD_PHI:
-      k_update_phi<<<grid_for(T.F), TPB, 0, st>>>(T, S.phi, S.Ee);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
 }
 
 template <int P, typename R>
@@ -968,6 +1236,23 @@ cudaError_t upload_reference_constants(const Tables& T) {
   for (int i = 0; i < 12 * Dm::NS * Dm::NEN; ++i) h.psiEc[i] = static_cast<R>(T.psiEc[i]);
   for (int i = 0; i < 12 * Dm::NEN; ++i) h.enode[i] = static_cast<unsigned char>(T.enode[i]);
   for (int i = 0; i < Dm::M * Dm::M; ++i) h.R_[i] = static_cast<R>(T.R[i]);
+  // row form of D^alpha, padded to RL entries per row with zeros (column = the row)
+  for (int al = 0; al < 3; ++al) {
+    int fill[Dm::N] = {};
+    for (int i = 0; i < Dm::N; ++i)
+      for (int sl = 0; sl < Dm::RL; ++sl) {
+        h.Eval[(al * Dm::RL + sl) * Dm::N + i] = R(0);
+        h.Ecol[(al * Dm::RL + sl) * Dm::N + i] = static_cast<unsigned char>(i);
+      }
+    for (int j = 0; j < Dm::N; ++j)
+      for (int t = T.Dptr[al * (Dm::N + 1) + j]; t < T.Dptr[al * (Dm::N + 1) + j + 1]; ++t) {
+        const int i = T.Drow[al * Dm::NNZ + t];
+        const int sl = fill[i]++;
+        if (sl >= Dm::RL) return cudaErrorInvalidValue;
+        h.Eval[(al * Dm::RL + sl) * Dm::N + i] = static_cast<R>(T.Dval[al * Dm::NNZ + t]);
+        h.Ecol[(al * Dm::RL + sl) * Dm::N + i] = static_cast<unsigned char>(j);
+      }
+  }
   return cudaMemcpyToSymbol(RC<P, R>::sym(), &h, sizeof(h));
 }
 
@@ -985,7 +1270,19 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
       k_bperp<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp);
       break;
     case ST_ADER:
-      k_ader<P, R><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+      if (T.predictor == 1) {
+        constexpr int ZB = Team<P>::ZB;
+        const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
+        if (T.positivity)
+          k_ader_team<P, R, true><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+        else
+          k_ader_team<P, R, false><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+      } else if (T.positivity) {
+        k_ader<P, R, true><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+        k_pos_traces<P, R><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, trF, trE);
+      } else {
+        k_ader<P, R, false><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+      }
       break;
     case ST_FACE:
       k_face_flux<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, trF, S.Ff, dt);
@@ -1015,6 +1312,29 @@ GEO_INSTANTIATE(2, float)
 GEO_INSTANTIATE(3, float)
 GEO_INSTANTIATE(4, float)
 #undef GEO_INSTANTIATE
+
+template <int P>
+cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState& A, double dt, cudaStream_t st) {
+  const double* Wc = static_cast<const double*>(S.Wc);
+  const double* Bp = static_cast<const double*>(S.Bp);
+  const double* trF = static_cast<const double*>(S.trF);
+  const double* trE = static_cast<const double*>(S.trE);
+  k_adj_cot<<<grid_for(T.F + T.E), TPB, 0, st>>>(T, A);
+  k_adj_face<P><<<grid_for(T.F), TPB, 0, st>>>(T, trF, A, dt);
+  k_adj_edge<P><<<grid_for(T.E), TPB, 0, st>>>(T, trE, A, dt);
+  k_adj_ader<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.phi, Wc, Bp, A, dt);
+  k_adj_bperp<P><<<grid_for(T.F), TPB, 0, st>>>(T, S.phi, Wc, A);
+  k_adj_weno<P><<<grid_for(T.Z), TPB, 0, st>>>(T, A);
+  return cudaGetLastError();
+}
+template cudaError_t launch_adjoint<2>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
+template cudaError_t launch_adjoint<3>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
+template cudaError_t launch_adjoint<4>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
+
+cudaError_t launch_outer_br2(const DevTables& T, const double* phi, double* out_dev, double* gphi, cudaStream_t st) {
+  k_outer_br2<<<1, 256, 0, st>>>(T, phi, out_dev, gphi);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cfl(const DevTables& T, const DevState& S, double cfl, double* out_host, cudaStream_t st) {
   int nb = reduction_blocks(T.Z);

@@ -1,0 +1,202 @@
+// Device helpers shared by the forward kernels (kernels.cu) and the adjoint
+// kernels (adjoint.cu): ideal MHD fluxes in rationalised units (Eq. 2.2), the
+// HLL solver, the Rusanov speed, MinMod, and the face/zone index maps.
+#pragma once
+#include "device.cuh"
+
+namespace geo {
+namespace dev {
+
+constexpr int TPB = 128;
+
+template <typename R> __device__ __forceinline__ const BulkTables<R>& bulk(const DevTables& T);
+template <> __device__ __forceinline__ const BulkTables<double>& bulk<double>(const DevTables& T) { return T.b64; }
+template <> __device__ __forceinline__ const BulkTables<float>& bulk<float>(const DevTables& T) { return T.b32; }
+
+// ----------------------------------------------------------------------------
+// ideal MHD (Eq. 2.2 in rationalised units), in the bulk type R
+// ----------------------------------------------------------------------------
+template <typename R>
+struct Prim {
+  R rho, vx, vy, vz, p, bx, by, bz;
+};
+
+template <typename R>
+__device__ __forceinline__ Prim<R> to_prim(const R* u, R g) {
+  Prim<R> w;
+  w.rho = u[0];
+  R ir = R(1) / u[0];
+  w.vx = u[1] * ir;
+  w.vy = u[2] * ir;
+  w.vz = u[3] * ir;
+  w.bx = u[5];
+  w.by = u[6];
+  w.bz = u[7];
+  w.p = (g - R(1)) * (u[4] - R(0.5) * w.rho * (w.vx * w.vx + w.vy * w.vy + w.vz * w.vz) -
+                      R(0.5) * (w.bx * w.bx + w.by * w.by + w.bz * w.bz));
+  return w;
+}
+
+// F(U).n for any vector n
+template <typename R>
+__device__ __forceinline__ void flux_n(const R* u, const Prim<R>& w, R nx, R ny, R nz, R* F) {
+  R vn = w.vx * nx + w.vy * ny + w.vz * nz;
+  R bn = w.bx * nx + w.by * ny + w.bz * nz;
+  R pt = w.p + R(0.5) * (w.bx * w.bx + w.by * w.by + w.bz * w.bz);
+  R vb = w.vx * w.bx + w.vy * w.by + w.vz * w.bz;
+  F[0] = w.rho * vn;
+  F[1] = u[1] * vn + pt * nx - w.bx * bn;
+  F[2] = u[2] * vn + pt * ny - w.by * bn;
+  F[3] = u[3] * vn + pt * nz - w.bz * bn;
+  F[4] = (u[4] + pt) * vn - bn * vb;
+  F[5] = w.bx * vn - w.vx * bn;
+  F[6] = w.by * vn - w.vy * bn;
+  F[7] = w.bz * vn - w.vz * bn;
+}
+
+template <typename R>
+__device__ __forceinline__ R fast_speed(const Prim<R>& w, R nx, R ny, R nz, R g) {
+  R ir = R(1) / w.rho;
+  R a2 = g * w.p * ir;
+  R b2 = (w.bx * w.bx + w.by * w.by + w.bz * w.bz) * ir;
+  R bn = w.bx * nx + w.by * ny + w.bz * nz;
+  R bn2 = bn * bn * ir;
+  R s = a2 + b2;
+  return sqrt(R(0.5) * (s + sqrt(fmax(s * s - R(4) * a2 * bn2, R(0)))));
+}
+
+// HLL flux along the unit normal (Davis wave speeds); the weighted flux is
+// accumulated in FP64
+template <typename R>
+__device__ __forceinline__ void hll_acc(const R* uL, const R* uR, R nx, R ny, R nz, R g, double w,
+                                        double* acc) {
+  Prim<R> a = to_prim(uL, g), b = to_prim(uR, g);
+  R vnL = a.vx * nx + a.vy * ny + a.vz * nz;
+  R vnR = b.vx * nx + b.vy * ny + b.vz * nz;
+  R cL = fast_speed(a, nx, ny, nz, g), cR = fast_speed(b, nx, ny, nz, g);
+  R SL = fmin(vnL - cL, vnR - cR);
+  R SR = fmax(vnL + cL, vnR + cR);
+  R FL[8], FR[8];
+  flux_n(uL, a, nx, ny, nz, FL);
+  flux_n(uR, b, nx, ny, nz, FR);
+  if (SL >= R(0)) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FL[v]);
+  } else if (SR <= R(0)) {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FR[v]);
+  } else {
+    R id = R(1) / (SR - SL);
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+      acc[v] += w * static_cast<double>((SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * id);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R rusanov_speed(const R* u, R nx, R ny, R nz, R g) {
+  Prim<R> w = to_prim(u, g);
+  return fabs(w.vx * nx + w.vy * ny + w.vz * nz) + fast_speed(w, nx, ny, nz, g);
+}
+
+template <typename R>
+__device__ __forceinline__ R minmod(R a, R b) {
+  if (a * b > R(0)) return (a > R(0) ? R(1) : R(-1)) * fmin(fabs(a), fabs(b));
+  return R(0);
+}
+
+// Positivity scaling (Zhang-Shu type) of point states toward the zone mean: the
+// factor theta <= 1 keeps rho >= eps_rho and p >= eps_p at every point, using the
+// concavity of p in the conserved variables for the pressure bound.
+template <typename R>
+__device__ __forceinline__ R pressure_of(const R* u, R g) {
+  const R ir = R(1) / u[0];
+  return (g - R(1)) * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir -
+                       R(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]));
+}
+
+struct PosAcc {
+  double th_r = 1.0, th_p = 1.0;
+};
+
+template <typename R>
+__device__ __forceinline__ void pos_rho(const R* s, const R* mean, R eps_r, R& th_r) {
+  if (s[0] < eps_r) th_r = fmin(th_r, (mean[0] - eps_r) / (mean[0] - s[0]));
+}
+
+template <typename R>
+__device__ __forceinline__ void pos_p(const R* s, const R* mean, R th_r, R g, R pb, R eps_p, R& th_p) {
+  R s1[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) s1[v] = mean[v] + th_r * (s[v] - mean[v]);
+  const R p1 = pressure_of(s1, g);
+  if (p1 < eps_p) th_p = fmin(th_p, (pb - eps_p) / (pb - p1));
+}
+
+// predictor traces, structure of arrays: value v of point idx at Gauss time m of
+// zone z sits at trF_at(z, m, idx, Z) + v * Z (consecutive zones are adjacent)
+template <int P>
+__device__ __forceinline__ size_t trF_at(long long z, int m, int idx, long long Z) {
+  return (static_cast<size_t>((m - 1) * Dim<P>::NQT + idx) * 8) * Z + z;
+}
+template <int P>
+__device__ __forceinline__ size_t trE_at(long long z, int m, int idx, long long Z) {
+  return (static_cast<size_t>((m - 1) * 12 * Dim<P>::NS + idx) * 8) * Z + z;
+}
+
+__device__ __forceinline__ int side_of_lf(int lf) { return lf == 0 ? 3 : (lf == 1 ? 1 : (lf == 2 ? 0 : 2)); }
+
+template <int P>
+__device__ __forceinline__ int foff(int lf) {
+  using Dm = Dim<P>;
+  return lf < 4 ? lf * Dm::NQS : 4 * Dm::NQS + (lf - 4) * Dm::NQR;
+}
+template <int P>
+__device__ __forceinline__ int nq_of(int lf) {
+  return lf < 4 ? Dim<P>::NQS : Dim<P>::NQR;
+}
+
+// face f -> L zone / local face, R zone / local face (-1 when on the boundary),
+// the column and local face whose tables hold the face geometry, shell index k
+struct FaceInfo {
+  long long zL, zR;
+  int lfL, lfR, cg, lfg, k, se;
+  double gsign;  // canonical normal = gsign * outward normal of (cg, lfg)
+};
+
+__device__ __forceinline__ FaceInfo face_info(const DevTables& T, long long f) {
+  FaceInfo fi;
+  int nr = T.nr;
+  if (f < T.F_rad) {
+    int c = static_cast<int>(f / (nr + 1));
+    int k = static_cast<int>(f % (nr + 1));
+    fi.zL = (k >= 1) ? static_cast<long long>(c) * nr + k - 1 : -1;
+    fi.zR = (k < nr) ? static_cast<long long>(c) * nr + k : -1;
+    fi.lfL = 5;
+    fi.lfR = 4;
+    fi.cg = c;
+    fi.lfg = 4;
+    fi.gsign = -1.0;
+    fi.k = k;
+    fi.se = -1;
+  } else {
+    long long r = f - T.F_rad;
+    int se = static_cast<int>(r / nr);
+    int k = static_cast<int>(r % nr);
+    int cL = T.se_col[2 * se], cR = T.se_col[2 * se + 1];
+    fi.zL = static_cast<long long>(cL) * nr + k;
+    fi.zR = static_cast<long long>(cR) * nr + k;
+    fi.lfL = T.se_lf[2 * se];
+    fi.lfR = T.se_lf[2 * se + 1];
+    fi.cg = cL;
+    fi.lfg = fi.lfL;
+    fi.gsign = 1.0;
+    fi.k = k;
+    fi.se = se;
+  }
+  return fi;
+}
+
+
+}  // namespace dev
+}  // namespace geo

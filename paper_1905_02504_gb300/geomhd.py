@@ -36,6 +36,8 @@ _SIGS = {
     "geo_mesh_destroy": [_h],
     "geo_mesh_sizes": [_h, _pi64, _pi64, _pi64],
     "geo_set_gamma": [_h, _d],
+    "geo_set_positivity": [_h, ctypes.c_int],
+    "geo_set_predictor": [_h, ctypes.c_int],
     "geo_zone_cubature": [_h, ctypes.c_int, _vp, _vp],
     "geo_edge_quadrature": [_h, ctypes.c_int, _vp, _vp],
     "geo_phi_from_edge_circulation": [_h, _vp, _vp],
@@ -51,6 +53,8 @@ _SIGS = {
     "geo_probe_fma_peak": [ctypes.c_int, _vp, _pd],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_cfl_dt_noalloc": [_h, _vp, _d, _vp],
+    "geo_step_adjoint": [_h, _d, _vp, _vp, _vp, _vp, _vp, _vp],
+    "geo_outer_Br2": [_h, _vp, _pd, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -104,6 +108,18 @@ def geo_mesh_sizes(h):
 
 def geo_set_gamma(h, gamma):
     _check(_lib.geo_set_gamma(h, gamma), "geo_set_gamma")
+
+
+def geo_set_positivity(h, enable):
+    _check(_lib.geo_set_positivity(h, int(enable)), "geo_set_positivity")
+
+
+GEO_PRED_ZONE_THREAD = 0
+GEO_PRED_NODE_TEAM = 1
+
+
+def geo_set_predictor(h, schedule):
+    _check(_lib.geo_set_predictor(h, int(schedule)), "geo_set_predictor")
 
 
 def geo_zone_cubature(h, nq):
@@ -202,6 +218,21 @@ def geo_cfl_dt_noalloc(h, U_dev, cfl, dt_dev):
     float64 tensors; only enqueues work on the mesh stream."""
     assert _is_device(U_dev) and _is_device(dt_dev)
     _check(_lib.geo_cfl_dt_noalloc(h, _ptr(U_dev), cfl, _ptr(dt_dev)), "geo_cfl_dt_noalloc")
+
+
+def geo_step_adjoint(h, dt, U_in, phi_in, gU_out, gphi_out, gU_in, gphi_in):
+    """Cotangent at t from the cotangent at t+dt (all CUDA float64 tensors)."""
+    for t in (U_in, phi_in, gU_out, gphi_out, gU_in, gphi_in):
+        assert _is_device(t)
+    _check(_lib.geo_step_adjoint(h, dt, _ptr(U_in), _ptr(phi_in), _ptr(gU_out), _ptr(gphi_out),
+                                 _ptr(gU_in), _ptr(gphi_in)), "geo_step_adjoint")
+
+
+def geo_outer_Br2(h, phi_dev, gphi_dev=None):
+    J = _d()
+    _check(_lib.geo_outer_Br2(h, _ptr(phi_dev), ctypes.byref(J),
+                              _ptr(gphi_dev) if gphi_dev is not None else None), "geo_outer_Br2")
+    return J.value
 
 
 def geo_last_error():

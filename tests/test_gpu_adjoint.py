@@ -1,0 +1,196 @@
+"""Hand-written adjoint of the step against finite differences.
+
+* A generic linear functional of one step's output, J = <wU, U'> + <wphi, phi'>,
+  exercises the whole transposed Jacobian; its adjoint gradient is compared
+  along seeded random directions with fourth-order central differences of the GPU
+  FP64 forward step and of the FP64 oracle (eps = 1e-6, relative agreement 1e-6),
+  from zone averages with 10 % seeded noise.
+* The differentiation objective (outer-shell B_r^2 after a window of K steps,
+  with per-step checkpoints) through torch.autograd, against central differences
+  with eps = 1e-6.
+MinMod, the HLL wave-speed choices and the Rusanov max are kinks; directions whose
+central-difference stencil crosses one (detected with the oracle's branch
+signature) are counted separately and not compared.
+Directions for phi are discrete curls of random edge values (divergence-free).
+"""
+import numpy as np
+import pytest
+
+from conftest import gpu_available
+from test_gpu_parity import setup_case
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-6          # the configured central-difference step
+EPS_STEP = 1e-6     # one step, fourth-order stencil over +-h, +-2h
+ROUGH = 0.1         # seeded relative noise on the zone averages of the one-step check
+TOL = 1e-6
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not gpu_available():
+        pytest.skip("no CUDA device")
+
+
+def direction(o, U, rng):
+    """Per-variable scaled random direction for U; a curl direction for phi."""
+    m = o.mesh
+    scale = np.abs(U).mean(axis=0)
+    dU = rng.uniform(-1.0, 1.0, U.shape) * scale
+    dU[:, 5:8] = 0.0            # the zone B is overwritten by the reconstruction; probe it too below
+    a = rng.uniform(-1.0, 1.0, m.E) * 1e-2
+    dphi = (m.face_edge_sign * a[m.face_edges]).sum(1)
+    return dU, dphi
+
+
+def gpu_step(mesh, U, phi, dt):
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    Ut = torch.from_numpy(np.ascontiguousarray(U.T)).cuda()
+    pt = torch.from_numpy(phi.copy()).cuda()
+    geomhd.geo_state_upload(mesh.h, Ut, pt)
+    geomhd.geo_step(mesh.h, dt)
+    Uo = torch.empty_like(Ut)
+    po = torch.empty_like(pt)
+    geomhd.geo_state_download(mesh.h, Uo, po)
+    return Uo.cpu().numpy().T, po.cpu().numpy()
+
+
+def roughen(U, rng, amp=ROUGH):
+    """Seeded relative noise on every zone average.  In the smooth field the two
+    states of a face differ by little, so the Davis min/max choices, the Rusanov
+    max and MinMod sit next to their switch points (or on them: exact MinMod ties
+    of the symmetric field), and even a 1e-5 stencil crosses several.  With 10 %
+    noise the choices are clear and a +-2e-6 stencil crosses few or none."""
+    return U * (1.0 + amp * rng.uniform(-1.0, 1.0, U.shape))
+
+
+def branch_flips(o, U, phi, dU, dphi, dt, eps):
+    """Number of MinMod / HLL / max branch decisions of the oracle step that differ
+    between x + eps d and x - eps d (a central difference across a kink)."""
+    from oracle import physics
+    sigs = []
+    for s in (1.0, -1.0):
+        physics.BRANCHES = []
+        o.step(U + s * eps * dU, phi + s * eps * dphi, dt)
+        sigs.append(physics.BRANCHES)
+        physics.BRANCHES = None
+    return sum(int((a[1] != b[1]).sum()) for a, b in zip(*sigs))
+
+
+def central4(J, U, phi, dU, dphi, h):
+    """Fourth-order central difference (8 [J(h) - J(-h)] - [J(2h) - J(-2h)]) / 12h: its
+    truncation error is O(h^4); at h = 1e-6 it and the forward's rounding noise sit near
+    1e-8 relative, far below the 1e-6 tolerance."""
+    d1 = J(U + h * dU, phi + h * dphi) - J(U - h * dU, phi - h * dphi)
+    d2 = J(U + 2 * h * dU, phi + 2 * h * dphi) - J(U - 2 * h * dU, phi - 2 * h * dphi)
+    return (8.0 * d1 - d2) / (12.0 * h)
+
+
+@pytest.mark.parametrize("n,nr,p", [(5, 3, 2), (4, 4, 3), (3, 5, 4)])
+def test_adjoint_matches_finite_differences(n, nr, p):
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    o, mesh, U, phi = setup_case(n, nr, p)
+    rng = np.random.default_rng(1905 + p)
+    U = roughen(U, rng)
+    dt = o.cfl_dt(U, 0.4)
+    wU = rng.standard_normal(U.shape)
+    wphi = rng.standard_normal(phi.shape)
+    # adjoint gradient of J = <wU, U'> + <wphi, phi'>
+    U_in = torch.from_numpy(np.ascontiguousarray(U.T)).cuda()
+    phi_in = torch.from_numpy(phi.copy()).cuda()
+    gU = torch.empty_like(U_in)
+    gphi = torch.empty_like(phi_in)
+    geomhd.geo_step_adjoint(mesh.h, dt, U_in, phi_in, torch.from_numpy(np.ascontiguousarray(wU.T)).cuda(),
+                            torch.from_numpy(wphi.copy()).cuda(), gU, gphi)
+    torch.cuda.synchronize()
+    gU = gU.cpu().numpy().T
+    gphi = gphi.cpu().numpy()
+
+    def J_gpu(Ux, phix):
+        U1, p1 = gpu_step(mesh, Ux, phix, dt)
+        return (wU * (U1 - Ux)).sum() + (wphi * (p1 - phix)).sum()
+
+    def J_orc(Ux, phix):
+        U1, p1 = o.step(Ux, phix, dt)
+        return (wU * (U1 - Ux)).sum() + (wphi * (p1 - phix)).sum()
+
+    checked, crossing, oracle_checked = 0, 0, False
+    for trial in range(9):
+        dU, dphi = direction(o, U, rng)
+        if trial % 3 == 2:      # the zone B (helper) enters through the reconstruction
+            dU[:, 5:8] = rng.uniform(-1.0, 1.0, (U.shape[0], 3)) * np.abs(U[:, 5:8]).mean(0)
+        h = EPS_STEP
+        if branch_flips(o, U, phi, dU, dphi, dt, h) or branch_flips(o, U, phi, dU, dphi, dt, 2 * h):
+            crossing += 1       # reported separately: the central difference straddles a kink
+            continue
+        # compare the part of the derivative the step itself adds: the increment
+        # functional <wU, U' - U> + <wphi, phi' - phi> has gradient g - w
+        lin = (wU * dU).sum() + (wphi * dphi).sum()
+        adj = (gU * dU).sum() + (gphi * dphi).sum() - lin
+        fd = central4(J_gpu, U, phi, dU, dphi, h)
+        assert abs(adj - fd) <= TOL * abs(fd), (trial, adj, fd)
+        checked += 1
+        if not oracle_checked:
+            fdo = central4(J_orc, U, phi, dU, dphi, h)
+            assert abs(adj - fdo) <= TOL * abs(fdo), (adj, fdo)
+            oracle_checked = True
+    print("order %d: %d directions checked, %d crossed a branch switch" % (p, checked, crossing))
+    assert checked >= 3 and oracle_checked
+    mesh.close()
+
+
+def test_window_objective_gradient_with_checkpoints():
+    """J = integral of B_r^2 over the outer shell after K = 3 steps (order 3)."""
+    import torch
+    from paper_1905_02504_gb300 import autodiff, geomhd
+    o, mesh, U, phi = setup_case(4, 4, 3)
+    dt = o.cfl_dt(U, 0.4)
+    K = 3
+    eps = EPS
+    Ut = torch.from_numpy(np.ascontiguousarray(U.T)).cuda().requires_grad_(True)
+    pt = torch.from_numpy(phi.copy()).cuda().requires_grad_(True)
+    UK, pK = autodiff.step_window(mesh, Ut, pt, dt, K)
+    J = autodiff.outer_br2(mesh, pK)
+    J.backward()
+    gU = Ut.grad.cpu().numpy().T
+    gphi = pt.grad.cpu().numpy()
+    # objective definition check on the final state
+    m = o.mesh
+    outer = np.arange(m.ncol) * (m.nr + 1) + m.nr
+    area = o.dfb.area[m.face_L[outer, 0], 5]
+    assert abs(J.item() - (pK.detach().cpu().numpy()[outer] ** 2 / area).sum()) <= 1e-12 * J.item()
+
+    def J_of(Ux, phix):
+        with torch.no_grad():
+            a = torch.from_numpy(np.ascontiguousarray(Ux.T)).cuda()
+            b = torch.from_numpy(phix.copy()).cuda()
+            _, pk = autodiff.StepWindow.apply(a, b, mesh, dt, K)
+            return geomhd.geo_outer_Br2(mesh.h, pk)
+
+    def window_flips(dU, dphi):
+        from oracle import physics
+        sigs = []
+        for s in (1.0, -1.0):
+            physics.BRANCHES = []
+            Ux, px = U + s * eps * dU, phi + s * eps * dphi
+            for _ in range(K):
+                Ux, px = o.step(Ux, px, dt)
+            sigs.append(physics.BRANCHES)
+            physics.BRANCHES = None
+        return sum(int((a[1] != b[1]).sum()) for a, b in zip(*sigs))
+
+    rng = np.random.default_rng(64)
+    checked = 0
+    for _ in range(6):
+        dU, dphi = direction(o, U, rng)
+        if window_flips(dU, dphi):
+            continue
+        adj = (gU * dU).sum() + (gphi * dphi).sum()
+        fd = (J_of(U + eps * dU, phi + eps * dphi) - J_of(U - eps * dU, phi - eps * dphi)) / (2 * eps)
+        assert abs(adj - fd) <= TOL * abs(fd), (adj, fd)
+        checked += 1
+    assert checked >= 2
+    mesh.close()

@@ -23,18 +23,21 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-def fp32_mesh(n, nr, p, U, phi):
+def fp32_mesh(n, nr, p, U, phi, schedule=None):
     from paper_1905_02504_gb300 import geomhd
     m = geomhd.Mesh(n, nr, 1.0, 2.0, p, prec=geomhd.GEO_FP32_BULK)
+    if schedule is not None:
+        geomhd.geo_set_predictor(m.h, schedule)
     m.upload(np.ascontiguousarray(U.T), phi.copy())
     return m
 
 
-@pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 10), (4, 4, 3, 4), (3, 5, 4, 2)])
-def test_fp32_bulk_error_vs_oracle(n, nr, p, steps):
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 10), (5, 3, 3, 4), (3, 5, 4, 2)])
+def test_fp32_bulk_error_vs_oracle(n, nr, p, steps, schedule):
     o, m64, U, phi = setup_case(n, nr, p)
     m64.close()
-    m = fp32_mesh(n, nr, p, U, phi)
+    m = fp32_mesh(n, nr, p, U, phi, schedule)
     dt = o.cfl_dt(U, 0.4)
     for _ in range(steps):
         U, phi = o.step(U, phi, dt)
@@ -50,11 +53,13 @@ def test_fp32_bulk_error_vs_oracle(n, nr, p, steps):
     m.close()
 
 
-@pytest.mark.parametrize("p", [2, 3])
-def test_fp32_bulk_free_stream(p):
-    o, m64, U, phi = setup_case(4, 3, p, problem="uniform")
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_fp32_bulk_free_stream(p, schedule):
+    n, nr = (4, 3) if p < 4 else (3, 5)
+    o, m64, U, phi = setup_case(n, nr, p, problem="uniform")
     m64.close()
-    m = fp32_mesh(4, 3, p, U, phi)
+    m = fp32_mesh(n, nr, p, U, phi, schedule)
     dt = m.cfl_dt(0.3)
     for _ in range(3):
         m.step(dt)
