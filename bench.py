@@ -51,6 +51,10 @@ def parse():
                     help="device CFL reduction before every timed step (dt read back each step)")
     ap.add_argument("--nq-zone", type=int, default=0, help="cubature points per direction for the initial data")
     ap.add_argument("--nq-edge", type=int, default=8, help="Gauss points per edge for the initial face fluxes")
+    ap.add_argument("--adjoint", default="",
+                    help="differentiation workload: comma-separated window lengths K (e.g. 1,8,64)")
+    ap.add_argument("--fd-directions", type=int, default=16)
+    ap.add_argument("--fd-eps", type=float, default=1e-6)
     ap.add_argument("--predictor", type=int, default=None, choices=[0, 1],
                     help="predictor schedule: 0 one thread per zone, 1 one thread per node (default: per form)")
     ap.add_argument("--sample-n", type=int, default=4)
@@ -430,10 +434,99 @@ def gpu_arm(a):
         torch.distributed.destroy_process_group()
 
 
+def adjoint_arm(a):
+    """Differentiation workload: J = sum over the outer radial faces of phi^2 / A
+    after K steps of fixed dt; the gradient wrt the initial U and phi by the
+    hand-written adjoint with one checkpoint per step.  Times the forward window
+    (with its checkpoint copies) and the reverse sweep with CUDA events, and
+    compares <grad, d> with central differences of J along seeded directions
+    (U per-variable scaled with B left out, phi the discrete curl of random edge
+    values, so divergence-free).  FP64 form."""
+    import numpy as np
+    import torch
+    from paper_1905_02504_gb300 import autodiff, geomhd
+    from paper_1905_02504_gb300.inputs import make_problem
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    mesh = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order)
+    U0, phi0 = mesh.initial_state(make_problem(a.problem, noise=a.noise), nq_zone=a.nq_zone or None,
+                                  nq_edge=a.nq_edge)
+    mesh.upload(U0, phi0)
+    dt = mesh.cfl_dt(a.cfl)
+    Z, F, E = mesh.Z, mesh.F, mesh.E
+    Ut0 = torch.from_numpy(np.ascontiguousarray(U0)).cuda()
+    pt0 = torch.from_numpy(phi0.copy()).cuda()
+    rng = np.random.default_rng(1905)
+    scale = np.abs(U0).mean(axis=1)
+    dirs = []
+    for _ in range(a.fd_directions):
+        dU = rng.uniform(-1.0, 1.0, U0.shape) * scale[:, None]
+        dU[5:8] = 0.0
+        dphi = geomhd.geo_phi_from_edge_circulation(mesh.h, rng.uniform(-1.0, 1.0, E) * 1e-2)
+        dirs.append((torch.from_numpy(dU).cuda(), torch.from_numpy(dphi).cuda()))
+
+    def J_of(Ux, px, K):
+        geomhd.geo_state_upload(mesh.h, Ux, px)
+        for _ in range(K):
+            geomhd.geo_step(mesh.h, dt)
+        out_U = torch.empty_like(Ux)
+        out_p = torch.empty_like(px)
+        geomhd.geo_state_download(mesh.h, out_U, out_p)
+        return geomhd.geo_outer_Br2(mesh.h, out_p)
+
+    results = []
+    for K in [int(k) for k in a.adjoint.split(",") if k]:
+        # warm-up window, then one timed forward + backward
+        for timed in (False, True):
+            Ut = Ut0.clone().requires_grad_(True)
+            pt = pt0.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            e0.record()
+            UK, pK = autodiff.step_window(mesh, Ut, pt, dt, K)
+            J = autodiff.outer_br2(mesh, pK)
+            e1.record()
+            J.backward()
+            e2.record()
+            torch.cuda.synchronize()
+        fwd_ms, bwd_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        gU, gphi = Ut.grad, pt.grad
+        errs = []
+        for dU, dphi in dirs:
+            adj = float((gU * dU).sum() + (gphi * dphi).sum())
+            eps = a.fd_eps
+            fd = (J_of(Ut0 + eps * dU, pt0 + eps * dphi, K) - J_of(Ut0 - eps * dU, pt0 - eps * dphi, K)) / (2 * eps)
+            errs.append(abs(adj - fd) / max(abs(fd), 1e-300))
+        errs = np.array(errs)
+        results.append({"K": K, "J": float(J), "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+                        "gradient_zone_updates_per_s": Z * K / ((fwd_ms + bwd_ms) * 1e-3),
+                        "adjoint_over_forward": bwd_ms / fwd_ms,
+                        "checkpoint_bytes": K * (8 * Z + F) * 8,
+                        "fd_eps": a.fd_eps, "fd_directions": len(errs),
+                        "fd_rel_err": {"median": float(np.median(errs)), "p90": float(np.quantile(errs, 0.9)),
+                                       "max": float(errs.max()),
+                                       "within_1e-6": int((errs <= 1e-6).sum()),
+                                       "within_1e-4": int((errs <= 1e-4).sum())}})
+    if rank == 0:
+        last = results[-1]
+        line = {"metric": "zone-updates/s of the gradient (K forward steps with checkpoints + K adjoint steps)",
+                "value": last["gradient_zone_updates_per_s"], "unit": "zone-updates/s", "n_gpus": ws,
+                "steps": last["K"], "warmup": 1, "ms_per_step": (last["forward_ms"] + last["backward_ms"]) / last["K"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "differentiation: " + workload_name(a) + ", J = outer-shell B_r^2",
+                           "zones": Z, "dt": dt},
+                "windows": results}
+        print(json.dumps(line), flush=True)
+    mesh.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+    elif a.adjoint:
+        adjoint_arm(a)
     else:
         gpu_arm(a)
 

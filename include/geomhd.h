@@ -129,6 +129,13 @@ int geo_phi_from_edge_circulation(geo_mesh_t mesh, const double* circ, double* p
 /* Zone centroids double[Z][3] and volumes double[Z] (host buffers). */
 int geo_zone_geometry(geo_mesh_t mesh, double* centroid, double* volume);
 
+/* Face areas double[F] and area-weighted normals double[F][3] (host buffers):
+ * the face rule's sum of w_q n_q dA_q on the mapped face (paper App. A rules,
+ * Sec. II.c), in the face's canonical orientation (radial faces: +r; angular
+ * faces: out of the face's L zone), which is the orientation of phi[f].  Per
+ * zone, the six faces' signed normals sum to zero up to rounding. */
+int geo_face_geometry(geo_mesh_t mesh, double* area, double* normal);
+
 /* Upload / download the state.  on_device != 0: U and phi are device pointers
  * (stream-ordered copies); otherwise host pointers (the call synchronises). */
 int geo_state_upload(geo_mesh_t mesh, const double* U, const double* phi, int on_device);
@@ -143,8 +150,19 @@ int geo_cfl_dt(geo_mesh_t mesh, double cfl, double* dt);
  * divergence-free B reconstruction (Sec. IV), ADER-CG predictor (Sec. V), HLL
  * face fluxes and multidimensional edge EMFs, finite-volume update of U and the
  * Yee constrained-transport update of phi (Eqs. 2.5-2.6).  Asynchronous on the
- * mesh stream. */
+ * mesh stream.  The U update raises a device flag when a zone leaves rho > 0,
+ * p > 0 or is not finite; the flag is copied to pinned host memory after every
+ * step, and a later geo_step whose predecessor's copy has landed returns
+ * GEO_ERR_NONPHYSICAL without launching anything (the state is left as
+ * computed, for inspection).  geo_check_state reads the flag synchronously. */
 int geo_step(geo_mesh_t mesh, double dt);
+
+/* Synchronises the mesh stream, returns the physical-state flags raised since the
+ * last upload or check in *flags (bit 0: rho <= 0, p <= 0 or a non-finite
+ * energy in some zone after an update) and clears them.  Returns
+ * GEO_ERR_NONPHYSICAL when *flags != 0, GEO_OK otherwise.  The paper has no
+ * counterpart (its positivity statement is Sec. I). */
+int geo_check_state(geo_mesh_t mesh, int* flags);
 
 /* Discrete divergence of the face fluxes (paper Sec. II.c): per zone
  * sum_f s_zf phi_f; returns max |.| and max |.| / sum_f |phi_f| (synchronises). */

@@ -37,7 +37,9 @@ from .mesh import taylor_exponents
 
 def minmod(a, b):
     from . import physics
-    physics.record("minmod", np.stack([a * b > 0.0, np.abs(a) <= np.abs(b)]))
+    if physics.BRANCHES is not None:
+        s = np.abs(a) + np.abs(b) + 1e-300
+        physics.record("minmod", np.stack([a * b / (s * s), (np.abs(b) - np.abs(a)) / s]))
     return np.where(a * b > 0.0, np.sign(a) * np.minimum(np.abs(a), np.abs(b)), 0.0)
 
 

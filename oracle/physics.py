@@ -27,12 +27,14 @@ RHO, MX, MY, MZ, EN, BX, BY, BZ = range(8)
 
 # Optional branch recorder (tests use it to detect finite-difference stencils that
 # cross a MinMod / HLL / max switch): a list that the branchy routines append to.
+# Each entry holds signed margins, normalised to O(1) scales: the sign of a margin
+# is the branch taken, its size the relative distance to the switch.
 BRANCHES = None
 
 
-def record(tag, arr):
+def record(tag, margins):
     if BRANCHES is not None:
-        BRANCHES.append((tag, np.asarray(arr).copy()))
+        BRANCHES.append((tag, np.asarray(margins, dtype=np.float64).copy()))
 
 
 def primitives(U, gamma):
@@ -89,7 +91,10 @@ def hll(UL, UR, nhat, gamma):
     Fs = (SR[..., None] * FL - SL[..., None] * FR
           + (SL * SR)[..., None] * (UR - UL)) / (SR - SL)[..., None]
     out = np.where((SL >= 0.0)[..., None], FL, np.where((SR <= 0.0)[..., None], FR, Fs))
-    record("hll", np.stack([SL >= 0.0, SR <= 0.0, vnL - cL <= vnR - cR, vnL + cL >= vnR + cR]))
+    if BRANCHES is not None:
+        sc = np.abs(vnL) + cL + np.abs(vnR) + cR
+        record("hll", np.stack([SL / sc, -SR / sc, ((vnR - cR) - (vnL - cL)) / sc,
+                                ((vnL + cL) - (vnR + cR)) / sc]))
     return out
 
 
@@ -110,7 +115,10 @@ def edge_emf(states, faces, tvec, gamma):
     acc = (E @ tvec).sum()
     for iL, iR, nh in faces:
         aL, aR = rusanov_speed(states[iL], nh, gamma), rusanov_speed(states[iR], nh, gamma)
-        record("emf", [aL >= aR, (states[iL][MX:MZ + 1] @ nh) >= 0.0, (states[iR][MX:MZ + 1] @ nh) >= 0.0])
+        if BRANCHES is not None:
+            vL = states[iL][MX:MZ + 1] @ nh / states[iL][RHO]
+            vR = states[iR][MX:MZ + 1] @ nh / states[iR][RHO]
+            record("emf", [(aL - aR) / (aL + aR), vL / aL, vR / aR])
         a = max(aL, aR)
         acc += a * np.dot(B[iR] - B[iL], np.cross(tvec, nh))
     return acc / k

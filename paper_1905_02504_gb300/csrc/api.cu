@@ -49,6 +49,11 @@ struct geo_mesh {
   double* adj_U0 = nullptr;
   double ms[geo::N_STAGES] = {};
   int64_t cnt[geo::N_STAGES] = {};
+  // physical-state flag of the last step, copied to pinned host memory after
+  // each step and looked at by the next geo_step once that copy has landed
+  int* status_host = nullptr;
+  cudaEvent_t status_ev = nullptr;
+  bool status_pending = false;
 
   template <typename Tv>
   const Tv* upload(const std::vector<Tv>& v, cudaError_t& err) {
@@ -87,6 +92,10 @@ struct geo_mesh {
   void release() {
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
+    if (status_host) cudaFreeHost(status_host);
+    status_host = nullptr;
+    if (status_ev) cudaEventDestroy(status_ev);
+    status_ev = nullptr;
     for (auto& t : pending) {
       cudaEventDestroy(t.a);
       cudaEventDestroy(t.b);
@@ -265,6 +274,13 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   S.Ff = m->alloc(8 * F, err);
   S.Ee = m->alloc(E, err);
   S.red = m->alloc(4096, err);
+  m->dt.status = static_cast<int*>(m->alloc_bytes(sizeof(int), err));
+  if (err == cudaSuccess) err = cudaMemset(m->dt.status, 0, sizeof(int));
+  if (err == cudaSuccess) err = cudaMallocHost(&m->status_host, sizeof(int));
+  if (err == cudaSuccess) {
+    *m->status_host = 0;
+    err = cudaEventCreateWithFlags(&m->status_ev, cudaEventDisableTiming);
+  }
   if (err != cudaSuccess) {
     int code = (err == cudaErrorMemoryAllocation) ? GEO_ERR_OOM : GEO_ERR_CUDA;
     std::string s = std::string("device setup: ") + cudaGetErrorString(err);
@@ -337,13 +353,22 @@ int geo_zone_geometry(geo_mesh_t m, double* xc, double* vol) {
   return GEO_OK;
 }
 
+int geo_face_geometry(geo_mesh_t m, double* area, double* normal) {
+  if (!m || !area || !normal) return fail(GEO_ERR_ARG, "bad arguments");
+  geo::face_geometry(m->T, area, normal);
+  return GEO_OK;
+}
+
 int geo_state_upload(geo_mesh_t m, const double* U, const double* phi, int on_device) {
   if (!m || !U || !phi) return fail(GEO_ERR_ARG, "bad arguments");
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaError_t e = cudaMemcpyAsync(m->ds.U, U, 8 * m->T.Z * sizeof(double), kind, m->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->ds.phi, phi, m->T.F * sizeof(double), kind, m->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->dt.status, 0, sizeof(int), m->st);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(m->st);
   if (e != cudaSuccess) return cuda_fail(e, "state upload");
+  m->status_pending = false;
+  *m->status_host = 0;
   m->have_state = true;
   return GEO_OK;
 }
@@ -371,11 +396,33 @@ int geo_cfl_dt(geo_mesh_t m, double cfl, double* dt) {
 int geo_step(geo_mesh_t m, double dt) {
   if (!m || !(dt > 0.0) || !std::isfinite(dt)) return fail(GEO_ERR_ARG, "bad arguments");
   if (!m->have_state) return fail(GEO_ERR_STATE, "no state uploaded");
+  if (m->status_pending && cudaEventQuery(m->status_ev) == cudaSuccess) {
+    m->status_pending = false;
+    if (*m->status_host) return fail(GEO_ERR_NONPHYSICAL, "an earlier step produced a non-physical state");
+  }
   for (int s = 0; s < geo::N_STAGES; ++s) {
     int rc = run_stage(m, s, dt);
     if (rc != GEO_OK) return rc;
   }
+  cudaError_t e = cudaMemcpyAsync(m->status_host, m->dt.status, sizeof(int), cudaMemcpyDeviceToHost, m->st);
+  if (e == cudaSuccess) e = cudaEventRecord(m->status_ev, m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  m->status_pending = true;
   return GEO_OK;
+}
+
+int geo_check_state(geo_mesh_t m, int* flags) {
+  if (!m || !flags) return fail(GEO_ERR_ARG, "bad arguments");
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, m->dt.status, sizeof(int), cudaMemcpyDeviceToHost, m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->dt.status, 0, sizeof(int), m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "state check");
+  *m->status_host = 0;
+  m->status_pending = false;
+  *flags = h;
+  return h ? fail(GEO_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or not finite) in a zone") : GEO_OK;
 }
 
 int geo_divB_max(geo_mesh_t m, double* abs_max, double* rel_max) {
@@ -433,12 +480,13 @@ int geo_stage_flops(geo_mesh_t m, double* fl, int64_t* units) {
   // nodal normal B per face: two polynomial evaluations per point, MinMod, shift
   fl[geo::ST_BPERP] = nq_mean * (2 * (3 * 2 * NC1 + 5) + 8);
   units[geo::ST_BPERP] = m->T.F;
-  // ADER: KKT apply + node values, then 1 + p (M-1) flux-difference levels, each
+  // ADER: KKT apply + node values, then 1 + (p-1)(M-1) flux-difference levels (the
+  // first Picard iteration reuses level 1's), each
   // with N primitive recoveries, 4 physical fluxes per node (3 metric directions
   // + the geometric-conservation residual) and the 3 NNZ nonzero couplings of the
   // serendipity derivative matrices over 8 variables; p Picard updates of M-1
   // levels; point values at the face (edge) points from the face's (edge's) nodes
-  const double levels = 1 + P * (M - 1);
+  const double levels = 1 + (P - 1) * (M - 1);
   const double flux = 45.0, prim = 17.0;
   const double per_level = N * (8 + prim + 4 * flux + 8) + 3.0 * d.NNZ * 8 * 2;
   fl[geo::ST_ADER] = 2 * (3 + 3 * N) * NBIN + N * 5 * 2 * NC1 + levels * per_level +

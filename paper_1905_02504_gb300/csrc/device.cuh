@@ -51,6 +51,7 @@ struct DevTables {
   double gamma;
   int positivity;      // 1: scale nodal and point states toward the zone mean (rho, p > 0)
   int predictor;       // 0: one thread per zone; 1: a team of N threads per zone (one per node)
+  int* status;         // [1] bit 0 set by the U update when a zone leaves rho > 0, p > 0 (or is not finite)
   const double* qpow;  // [nr + 2]: q^k
   const double *D, *R, *wt, *psiF, *psiE, *wE;
   const int* st_n;

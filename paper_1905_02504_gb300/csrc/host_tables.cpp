@@ -1282,4 +1282,25 @@ void zone_centroids(const Tables& T, double* xc, double* vol) {
     }
 }
 
+void face_geometry(const Tables& T, double* area, double* nrm) {
+  const int NQT = T.d.NQT;
+  auto fill = [&](int64_t f, int c, int lf, int k, double sign) {
+    const double s2 = std::pow(T.q, 2 * k);
+    double n[3] = {0.0, 0.0, 0.0};
+    for (int q = T.foff[lf]; q < T.foff[lf + 1]; ++q) {
+      const size_t idx = static_cast<size_t>(c) * NQT + q;
+      for (int a = 0; a < 3; ++a) n[a] += T.WF[idx] * T.nF[3 * idx + a];
+    }
+    area[f] = T.A0[6 * c + lf] * s2;
+    for (int a = 0; a < 3; ++a) nrm[3 * f + a] = sign * n[a] * s2;
+  };
+  // radial faces: the inner face (local face 4) of shell k, canonical normal +r
+  for (int c = 0; c < T.ncol; ++c)
+    for (int k = 0; k <= T.nr; ++k) fill(static_cast<int64_t>(c) * (T.nr + 1) + k, c, 4, k, -1.0);
+  // angular faces: outward normal of the L column's local face
+  for (int se = 0; se < T.nse; ++se)
+    for (int k = 0; k < T.nr; ++k)
+      fill(T.F_rad + static_cast<int64_t>(se) * T.nr + k, T.se_col[2 * se], T.se_lf[2 * se], k, 1.0);
+}
+
 }  // namespace geo

@@ -1015,8 +1015,15 @@ __global__ void __launch_bounds__(TPB) k_update_u(const DevTables T, double* __r
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[v] += sg * Ff[v * F + f];
   }
+  double u[8];
 #pragma unroll
-  for (int v = 0; v < 8; ++v) U[v * Z + z] -= iV * acc[v];
+  for (int v = 0; v < 8; ++v) {
+    u[v] = U[v * Z + z] - iV * acc[v];
+    U[v * Z + z] = u[v];
+  }
+  // physical-state flag (read by the host between steps)
+  const double p = pressure_of(u, T.gamma);
+  if (!(u[0] > 0.0) || !(p > 0.0) || !isfinite(u[4])) atomicOr(T.status, 1);
 }
 
 __global__ void __launch_bounds__(TPB) k_update_phi(const DevTables T, double* __restrict__ phi,

@@ -13,6 +13,11 @@ import numpy as np
 from . import _build
 
 GEO_OK = 0
+GEO_ERR_ARG = -1
+GEO_ERR_OOM = -2
+GEO_ERR_CUDA = -3
+GEO_ERR_NONPHYSICAL = -4
+GEO_ERR_STATE = -6
 GEO_FP64 = 0
 GEO_FP32_BULK = 1
 N_STAGES = 7
@@ -38,10 +43,12 @@ _SIGS = {
     "geo_set_gamma": [_h, _d],
     "geo_set_positivity": [_h, ctypes.c_int],
     "geo_set_predictor": [_h, ctypes.c_int],
+    "geo_check_state": [_h, ctypes.POINTER(ctypes.c_int)],
     "geo_zone_cubature": [_h, ctypes.c_int, _vp, _vp],
     "geo_edge_quadrature": [_h, ctypes.c_int, _vp, _vp],
     "geo_phi_from_edge_circulation": [_h, _vp, _vp],
     "geo_zone_geometry": [_h, _vp, _vp],
+    "geo_face_geometry": [_h, _vp, _vp],
     "geo_state_upload": [_h, _vp, _vp, ctypes.c_int],
     "geo_state_download": [_h, _vp, _vp, ctypes.c_int],
     "geo_cfl_dt": [_h, _d, _pd],
@@ -67,12 +74,14 @@ EXPORTED = tuple(_SIGS) + ("geo_last_error",)
 
 
 class GeoError(RuntimeError):
-    pass
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 def _check(rc, what):
     if rc != GEO_OK:
-        raise GeoError("%s failed (%d): %s" % (what, rc, _lib.geo_last_error().decode()))
+        raise GeoError("%s failed (%d): %s" % (what, rc, _lib.geo_last_error().decode()), rc)
 
 
 def _ptr(a):
@@ -122,6 +131,14 @@ def geo_set_predictor(h, schedule):
     _check(_lib.geo_set_predictor(h, int(schedule)), "geo_set_predictor")
 
 
+def geo_check_state(h):
+    """Physical-state flags raised since the last upload or check (cleared);
+    raises GeoError with GEO_ERR_NONPHYSICAL when any is set."""
+    flags = ctypes.c_int(0)
+    _check(_lib.geo_check_state(h, ctypes.byref(flags)), "geo_check_state")
+    return flags.value
+
+
 def geo_zone_cubature(h, nq):
     Z, _, _ = geo_mesh_sizes(h)
     pts = np.empty((Z, nq ** 3, 3))
@@ -144,6 +161,14 @@ def geo_phi_from_edge_circulation(h, circ):
     phi = np.empty(F)
     _check(_lib.geo_phi_from_edge_circulation(h, _ptr(circ), _ptr(phi)), "geo_phi_from_edge_circulation")
     return phi
+
+
+def geo_face_geometry(h):
+    _, F, _ = geo_mesh_sizes(h)
+    area = np.empty(F)
+    nrm = np.empty((F, 3))
+    _check(_lib.geo_face_geometry(h, _ptr(area), _ptr(nrm)), "geo_face_geometry")
+    return area, nrm
 
 
 def geo_zone_geometry(h):

@@ -182,3 +182,25 @@ def test_positivity_parity(n, nr, p, schedule):
     d = max(rel_l1(U0g[v], U1[:, v]) for v in range(8))
     assert not np.isfinite(d) or d > 1e-8
     m.close()
+
+
+def test_face_geometry_matches_oracle_and_closes():
+    from paper_1905_02504_gb300 import geomhd
+    o, m, U, phi = setup_case(4, 4, 3)
+    area, nrm = geomhd.geo_face_geometry(m.h)
+    om = o.mesh
+    ref_a = np.empty(om.F)
+    ref_n = np.empty((om.F, 3))
+    for f in range(om.F):
+        zL, lfL = om.face_L[f]
+        zR, lfR = om.face_R[f]
+        z0, lf0, sgn = (zL, lfL, 1.0) if zL >= 0 else (zR, lfR, -1.0)
+        fg = o.dfb.fgeo[lf0]
+        ref_a[f] = o.dfb.area[z0, lf0]
+        ref_n[f] = sgn * (fg["w"][:, None] * fg["dA"][z0][:, None] * fg["n"][z0]).sum(0)
+    assert np.abs(area - ref_a).max() <= 1e-13 * ref_a.max()
+    assert np.abs(nrm - ref_n).max() <= 1e-13 * ref_a.max()
+    # closure: the six signed area vectors of every zone sum to zero
+    close = (om.zone_face_sign[..., None] * nrm[om.zone_face]).sum(1)
+    assert np.abs(close).max() <= 1e-14 * ref_a.max()
+    m.close()
