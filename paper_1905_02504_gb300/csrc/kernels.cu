@@ -488,11 +488,40 @@ template <> struct Team<2> { static constexpr int ZB = 16; };
 template <> struct Team<3> { static constexpr int ZB = 8; };
 template <> struct Team<4> { static constexpr int ZB = 4; };
 
+// 8-vectors in shared memory are split into 16-byte chunks stored chunk-major,
+// [alpha][chunk][node] within a zone.  Threads are mapped zone-fastest (thread =
+// node * ZB + zone), so the 8 threads of a quarter warp, which share one 16-byte
+// access phase, handle the same node (P = 2, 3) or two nodes (P = 4) of several
+// zones; the per-zone stride XS is padded to 1 (2) modulo the 8 bank groups so
+// that those zones' copies of one chunk sit in distinct bank groups.
+template <typename R> struct Chunk { static constexpr int CH = 16 / sizeof(R), NCH = 8 / CH; };
+
+template <typename R>
+__device__ __forceinline__ void ld16(const R* p, R* out) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
+  } else {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    out[0] = q.x; out[1] = q.y;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void st16(R* p, const R* in) {
+  if constexpr (sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(in[0], in[1], in[2], in[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(in[0], in[1]);
+  }
+}
+
 template <int P, typename R>
 struct TeamSmem {
   using Dm = Dim<P>;
-  static constexpr int ZB = Team<P>::ZB;
-  alignas(16) R X[ZB][3][Dm::N][8];  // fluxes of one level / the final levels
+  static constexpr int ZB = Team<P>::ZB, CH = Chunk<R>::CH, NCH = Chunk<R>::NCH;
+  static constexpr int XS0 = 3 * NCH * Dm::N, XT = ZB >= 8 ? 1 : 2;
+  static constexpr int XS = XS0 + ((XT - XS0 % 8) + 8) % 8;  // chunks per zone, XS % 8 == XT
+  alignas(16) R X[ZB][XS][CH];       // fluxes of one level / the final levels
   R in[ZB][Dm::NBIN];                // inputs of the divergence-free reconstruction
   R W[ZB][5 * Dm::NC1];              // fluid Taylor coefficients
   R Uz[ZB][8];                       // zone means (B: the divergence-free mean)
@@ -500,6 +529,7 @@ struct TeamSmem {
   R psiF[Dm::NQT * Dm::NFN];
   R psiE[12 * Dm::NS * Dm::NEN];
   R th[ZB][4];                       // positivity factors (min-reduced)
+  R fs[ZB];                          // dt l_0 / l_k of the zone (Eq. 5.21)
   unsigned char Ec[3 * Dm::RL * Dm::N];
   unsigned char fnode[6 * Dm::NFN];
   unsigned char enode[12 * Dm::NEN];
@@ -514,13 +544,14 @@ __device__ __forceinline__ void smem_min_nonneg(double* a, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
-// one flux difference of node i of a team: dF = sum_alpha sum_j D^alpha_ij F^alpha_j - F_i . g_i
+// one flux difference of node i of a team: dF = sum_alpha sum_j D^alpha_ij F^alpha_j - F_i . g_i;
+// X is the zone's exchange buffer, chunk (alpha * NCH + c) * N + node
 template <int P, typename R>
 __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, const R* g, const R* Sa, R gam,
-                                                     R (*X)[Dim<P>::N][8], const R* Ev, const unsigned char* Ec,
+                                                     R (*X)[Chunk<R>::CH], const R* Ev, const unsigned char* Ec,
                                                      int i, bool valid) {
   using Dm = Dim<P>;
-  constexpr int N = Dm::N, RL = Dm::RL;
+  constexpr int N = Dm::N, RL = Dm::RL, CH = Chunk<R>::CH, NCH = Chunk<R>::NCH;
   if (valid) {
     R u[8];
 #pragma unroll
@@ -535,7 +566,7 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
       R Fa[8];
       flux_n(u, w, Sa[3 * al], Sa[3 * al + 1], Sa[3 * al + 2], Fa);
 #pragma unroll
-      for (int v = 0; v < 8; ++v) X[al][i][v] = Fa[v];
+      for (int c = 0; c < NCH; ++c) st16(&X[(al * NCH + c) * N + i][0], &Fa[c * CH]);
     }
   }
   __syncthreads();
@@ -545,16 +576,32 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
 #pragma unroll
       for (int sl = 0; sl < RL; ++sl) {
         const R d = Ev[(al * RL + sl) * N + i];
-        const R* Fj = X[al][Ec[(al * RL + sl) * N + i]];
+        if (d != R(0)) {  // padding entries of short rows: no shared-memory traffic
+          const int j = Ec[(al * RL + sl) * N + i];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) dF[v] += d * Fj[v];
+          for (int c = 0; c < NCH; ++c) {
+            R f[CH];
+            ld16(&X[(al * NCH + c) * N + j][0], f);
+#pragma unroll
+            for (int t = 0; t < CH; ++t) dF[c * CH + t] += d * f[t];
+          }
+        }
       }
   }
   __syncthreads();
 }
 
+// resident blocks per SM the register budget is sized for
+template <int P, typename R> struct TeamOcc;
+template <> struct TeamOcc<2, float> { static constexpr int MINB = 8; };   // 128 threads
+template <> struct TeamOcc<3, float> { static constexpr int MINB = 4; };   // 160 threads
+template <> struct TeamOcc<4, float> { static constexpr int MINB = 3; };   // 128 threads
+template <> struct TeamOcc<2, double> { static constexpr int MINB = 4; };
+template <> struct TeamOcc<3, double> { static constexpr int MINB = 2; };
+template <> struct TeamOcc<4, double> { static constexpr int MINB = 2; };
+
 template <int P, typename R, bool POS>
-__global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
+__global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
     k_ader_team(const DevTables T, double* __restrict__ U, const double* __restrict__ phi,
                 const R* __restrict__ Wc, const R* __restrict__ Bp, R* __restrict__ trF, R* __restrict__ trE,
                 double dt) {
@@ -631,15 +678,15 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
       for (int b = 0; b < NBIN; ++b) s += GB[b * NR + d] * S.in[zl][b];
       S.Uz[zl][5 + d] = s;
       U[(5 + d) * Z + z] = static_cast<double>(s);
+      if (d == 0) S.fs[zl] = static_cast<R>(dt / T.qpow[z % nr]);  // one FP64 division per zone
     }
   }
   __syncthreads();
-  // ---- node of this thread
-  const int zl = tid / N, i = tid % N;
+  // ---- node of this thread (zone-fastest mapping)
+  const int zl = tid % ZB, i = tid / ZB;
   const long long z = zbase + zl;
   const bool valid = z < Z;
   const int c = valid ? static_cast<int>(z / nr) : 0;
-  const int k = valid ? static_cast<int>(z % nr) : 0;
   const R gam = static_cast<R>(T.gamma);
   R Uh[M][8];
   {
@@ -703,8 +750,9 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
   }
   // ---- Picard iterations (Eqs. C.34-C.36); in the first iteration every level
   // equals level 1, so its flux difference is reused
-  const R fs = static_cast<R>(dt / T.qpow[k]);
-  R (*X)[N][8] = S.X[zl];
+  const R fs = S.fs[zl];
+  constexpr int CH = Chunk<R>::CH, NCH = Chunk<R>::NCH;
+  R (*X)[CH] = S.X[zl];
   R dF[M][8];
   team_flux_difference<P, R>(Uh[0], dF[0], iJ, g, Sa, gam, X, S.Ev, S.Ec, i, valid);
 #pragma unroll
@@ -736,7 +784,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
 #pragma unroll
   for (int m = 1; m < M; ++m)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) X[m - 1][i][v] = Uh[m][v];
+    for (int c = 0; c < NCH; ++c) st16(&X[((m - 1) * NCH + c) * N + i][0], &Uh[m][c * CH]);
   __syncthreads();
   // ---- point values; thread -> (zone zl2 = tid % ZB, point slots tid / ZB + N s)
   {
@@ -747,7 +795,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
     const int c2 = valid2 ? static_cast<int>(z2 / nr) : 0;
     const R* JF = BT.JF + static_cast<size_t>(c2) * NQT;
     const R* JE = BT.JE + static_cast<size_t>(c2) * 12 * NS;
-    const R(*X2)[N][8] = S.X[zl2];
+    const R(*X2)[CH] = S.X[zl2];
     const R* Uz = S.Uz[zl2];
     constexpr int NPASS = POS ? 3 : 1;
     R pbar = R(0), eps_r = R(0), eps_p = R(0), th = R(1);
@@ -773,9 +821,14 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
 #pragma unroll
           for (int a = 0; a < Dm::NFN; ++a) {
             const R w = S.psiF[idx * Dm::NFN + a];
-            const R* x = X2[m][S.fnode[lf * Dm::NFN + a]];
+            const int nd = S.fnode[lf * Dm::NFN + a];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) s[v] += w * x[v];
+            for (int c = 0; c < NCH; ++c) {
+              R x[CH];
+              ld16(&X2[(m * NCH + c) * N + nd][0], x);
+#pragma unroll
+              for (int t = 0; t < CH; ++t) s[c * CH + t] += w * x[t];
+            }
           }
           const R ij = valid2 ? R(1) / JF[idx] : R(1);
 #pragma unroll
@@ -786,9 +839,14 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N)
 #pragma unroll
           for (int a = 0; a < Dm::NEN; ++a) {
             const R w = S.psiE[idx * Dm::NEN + a];
-            const R* x = X2[m][S.enode[le * Dm::NEN + a]];
+            const int nd = S.enode[le * Dm::NEN + a];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) s[v] += w * x[v];
+            for (int c = 0; c < NCH; ++c) {
+              R x[CH];
+              ld16(&X2[(m * NCH + c) * N + nd][0], x);
+#pragma unroll
+              for (int t = 0; t < CH; ++t) s[c * CH + t] += w * x[t];
+            }
           }
           const R ij = valid2 ? R(1) / JE[idx] : R(1);
 #pragma unroll
