@@ -100,10 +100,9 @@ int geo_set_positivity(geo_mesh_t mesh, int enable);
 /* Execution schedule of the predictor stage (a2 zone part + a3, Sec. IV.b steps
  * 8-10 and Eqs. C.34-C.36); both compute the same arithmetic:
  *   GEO_PRED_ZONE_THREAD (0): one thread per zone, its nodal states in
- *     thread-local memory (default of the FP64 form);
- *   GEO_PRED_NODE_TEAM (1): one thread per serendipity node, a team of N threads
- *     per zone exchanging nodal fluxes through shared memory (default of the
- *     FP32-bulk form).
+ *     thread-local memory;
+ *   GEO_PRED_NODE_TEAM (1, default): one thread per serendipity node, a team of
+ *     N threads per zone exchanging nodal fluxes through shared memory.
  * The two differ only in the summation order of the flux-difference rows.
  * Returns GEO_ERR_ARG for any other value. */
 enum { GEO_PRED_ZONE_THREAD = 0, GEO_PRED_NODE_TEAM = 1 };

@@ -19,7 +19,13 @@ which are not available.  Readings (the GPU path implements the same ones):
   * Smoothness: beta = sum_{1<=|a|<=p-1} <(d^a_s P)^2>_0, each multi-index a once.
   * AO combination (Balsara, Garain & Shu 2016 family):
       P = (w_H/g_H)(P_H - sum_k g_k P_k) + sum_k w_k P_k,
-    g_H = 0.85, g_k = 0.15/8, w_m = g_m/(beta_m + eps)^2 normalised, eps = 1e-12.
+    g_H = 0.85, g_k = 0.15/8, eps = 1e-12, and WENO-Z type nonlinear weights
+      w_m ~ g_m (1 + (tau / (beta_m + eps))^2),  tau = (1/8) sum_k |beta_H - beta_k|,
+    normalised.  Sec. VII states that the schemes reach their design accuracy from
+    the coarsest mesh on (Tables IIa-c); weights g_m/(beta_m + eps)^2 do not on the
+    configured meshes (their octant indicators differ from the central one by
+    tens of percent there, and the weights stay far from the linear ones), while
+    with tau the deviation from the linear weights is of third order in that spread.
   * Variables: all eight conserved components, componentwise (Sec. VI step 2).
   * Boundaries: ghost zones continue the log shells (geometry); their data are
     copies of the boundary shell (continuative outflow, Sec. VII).
@@ -27,7 +33,9 @@ which are not available.  Readings (the GPU path implements the same ones):
 Pinned by: tests/test_oracle_weno.py -- constants reproduced exactly; linear data
 reproduced exactly for every p; the central least-squares fit reproduces every
 polynomial of degree <= p-1 exactly on the curved mapped zones; smoothness of the
-central stencil equals the analytic integral for a known polynomial.
+central stencil equals the analytic integral for a known polynomial; the weights
+are exactly linear for equal indicators, deviate from linear at (at least) second
+order in the indicators' relative spread, and favour the smooth octants at a jump.
 parity unpinned (only by invariants): the constants g_H, g_k, eps and the
 stencil choices are readings, not values the paper fixes.
 """
@@ -40,6 +48,17 @@ from .mesh import taylor_exponents
 GAMMA_H = 0.85
 GAMMA_K = 0.15 / 8.0
 EPS = 1e-12
+
+
+def nonlinear_weights(bH, bK):
+    """Normalised WENO-AO weights from the central indicator bH (...) and the eight
+    octant indicators bK (..., 8): w_m ~ g_m (1 + (tau/(beta_m + eps))^2) with
+    tau the mean |bH - bK|."""
+    tau = np.abs(bH[..., None] - bK).mean(-1)
+    tH = GAMMA_H * (1.0 + (tau / (bH + EPS)) ** 2)
+    tK = GAMMA_K * (1.0 + (tau[..., None] / (bK + EPS)) ** 2)
+    tot = tH + tK.sum(-1)
+    return tH / tot, tK / tot[..., None]
 
 # local face -> side index (s, e, n, w) of the column
 LF_SIDE = {0: 3, 1: 1, 2: 0, 3: 2}
@@ -207,11 +226,14 @@ class WenoAO:
         uK = np.einsum("zoij,zojv->zovi", self.inv_oct, dO)       # (Z, 8oct, 8var, 3)
         bH = np.einsum("zvc,zcd,zvd->zv", uH, self.Q, uH)
         bK = (uK * uK).sum(-1)                                    # (Z, 8oct, 8var)
-        wH = GAMMA_H / (bH + EPS) ** 2
-        wK = GAMMA_K / (bK + EPS) ** 2
-        tot = wH + wK.sum(1)
-        wH = wH / tot
-        wK = wK / tot[:, None, :]
+        from . import physics
+        if physics.BRANCHES is not None:
+            # kinks of |bH - bK|; where both indicators are at rounding level the
+            # kink moves the weights by nothing (tau << eps), so it is not recorded
+            sb = bH[:, None, :] + bK
+            physics.record("weno", np.where(sb > 1e-24, (bH[:, None, :] - bK) / np.maximum(sb, 1e-300), 1.0))
+        wH, wK = nonlinear_weights(bH, np.moveaxis(bK, 1, -1))    # (Z, 8var), (Z, 8var, 8oct)
+        wK = np.moveaxis(wK, -1, 1)                               # (Z, 8oct, 8var)
         out = (wH / GAMMA_H)[..., None] * uH
         lin = uH[..., :3] - GAMMA_K * uK.sum(1)
         out[..., :3] = (wH / GAMMA_H)[..., None] * lin + (wK[..., None] * uK).sum(1)

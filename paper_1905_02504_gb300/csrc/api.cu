@@ -171,7 +171,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.E_rad = T.E_rad;
   D.gamma = 5.0 / 3.0;
   D.positivity = 0;
-  D.predictor = (prec == GEO_FP32_BULK) ? GEO_PRED_NODE_TEAM : GEO_PRED_ZONE_THREAD;
+  D.predictor = GEO_PRED_NODE_TEAM;
   std::vector<double> qpow(T.nr + 2);
   for (int k = 0; k < T.nr + 2; ++k) qpow[k] = std::pow(T.q, k);
   D.qpow = m->upload(qpow, err);

@@ -44,7 +44,8 @@ namespace {
 using namespace dev;
 
 // ----------------------------------------------------------------------------
-// a1: WENO-AO reconstruction (Sec. III)
+// a1: WENO-AO reconstruction (Sec. III); one thread per zone and conserved
+// variable (grid row y = variable)
 // ----------------------------------------------------------------------------
 template <int P, typename R>
 __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* __restrict__ U,
@@ -77,8 +78,8 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
   const R* pinv = B.pinvH + static_cast<size_t>(c) * NC1 * SMAX;
   const R* oinv = B.oct_inv + static_cast<size_t>(c) * 72;
   const R* Qm = B.Q + static_cast<size_t>(c) * NC1 * NC1;
-#pragma unroll 1
-  for (int v = 0; v < 8; ++v) {
+  {
+    const int v = blockIdx.y;  // one conserved variable per grid row
     const double* Uv = U + v * Z;
     const double u0d = Uv[z];
     const R u0 = static_cast<R>(u0d);
@@ -98,9 +99,8 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
       for (int j = 0; j < NC1; ++j) s += Qm[i * NC1 + j] * uH[j];
       bH += uH[i] * s;
     }
-    R wH = GH / ((bH + EPS) * (bH + EPS));
-    R tot = wH;
     R uK[8][3], wK[8];
+    R tau = R(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       R d0 = static_cast<R>(Uv[zo[3 * o]] - u0d), d1 = static_cast<R>(Uv[zo[3 * o + 1]] - u0d),
@@ -108,8 +108,18 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
       const R* A = oinv + 9 * o;
 #pragma unroll
       for (int a = 0; a < 3; ++a) uK[o][a] = A[3 * a] * d0 + A[3 * a + 1] * d1 + A[3 * a + 2] * d2;
-      R b = uK[o][0] * uK[o][0] + uK[o][1] * uK[o][1] + uK[o][2] * uK[o][2];
-      wK[o] = GK / ((b + EPS) * (b + EPS));
+      wK[o] = uK[o][0] * uK[o][0] + uK[o][1] * uK[o][1] + uK[o][2] * uK[o][2];  // beta_k for now
+      tau += fabs(bH - wK[o]);
+    }
+    // WENO-Z type weights g (1 + (tau / (beta + eps))^2), tau = mean |beta_H - beta_k|
+    tau *= R(0.125);
+    const R rH = tau / (bH + EPS);
+    R wH = GH * (R(1) + rH * rH);
+    R tot = wH;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const R r = tau / (wK[o] + EPS);
+      wK[o] = GK * (R(1) + r * r);
       tot += wK[o];
     }
     R itot = R(1) / tot;
@@ -1329,7 +1339,7 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
   R* trE = static_cast<R*>(S.trE);
   switch (stage) {
     case ST_WENO:
-      k_weno<P, R><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, Wc);
+      k_weno<P, R><<<dim3(grid_for(T.Z), 8), TPB, 0, st>>>(T, S.U, Wc);
       break;
     case ST_BPERP:
       k_bperp<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp);

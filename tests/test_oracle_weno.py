@@ -100,3 +100,25 @@ def test_octant_stencils_are_face_neighbours():
         assert set(map(tuple, st.central[z])) == nbs
         for o in range(8):
             assert set(map(tuple, st.octants[z][o])) <= nbs
+
+
+def test_nonlinear_weights_properties():
+    """The WENO-AO weights: exactly linear for equal indicators; their deviation
+    from the linear weights is at least second order in the indicators' relative
+    spread (tau / beta: third in fact, since tau / beta is common to all stencils
+    at first order); at a jump the octants that do not straddle it take the weight."""
+    from oracle.weno import GAMMA_H, GAMMA_K, nonlinear_weights
+    b = np.array([3e-3])
+    wH, wK = nonlinear_weights(b, np.full((1, 8), 3e-3))
+    assert wH[0] == GAMMA_H and np.all(wK == GAMMA_K)
+    rng = np.random.default_rng(5)
+    u = rng.uniform(-1.0, 1.0, (1, 8))
+    dev = []
+    for delta in (1e-2, 5e-3, 2.5e-3):
+        wH, wK = nonlinear_weights(b, b[:, None] * (1.0 + delta * u))
+        dev.append(max(abs(wH[0] / GAMMA_H - 1.0), np.abs(wK / GAMMA_K - 1.0).max()))
+    assert dev[0] / dev[1] > 3.5 and dev[1] / dev[2] > 3.5
+    # jump: the central stencil and four octants see it (beta ~ 1), four do not
+    bK = np.array([[1.0, 1e-6, 1.0, 1e-6, 1.0, 1e-6, 1.0, 1e-6]])
+    wH, wK = nonlinear_weights(np.array([1.0]), bK)
+    assert wK[0, 1::2].sum() > 0.999 and wH[0] < 1e-6
