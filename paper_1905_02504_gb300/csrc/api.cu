@@ -175,6 +175,13 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   std::vector<double> qpow(T.nr + 2);
   for (int k = 0; k < T.nr + 2; ++k) qpow[k] = std::pow(T.q, k);
   D.qpow = m->upload(qpow, err);
+  {
+    std::vector<double> iA0(T.A0.size()), iq2(T.nr + 2);
+    for (size_t i = 0; i < T.A0.size(); ++i) iA0[i] = 1.0 / T.A0[i];
+    for (int k = 0; k < T.nr + 2; ++k) iq2[k] = 1.0 / (qpow[k] * qpow[k]);
+    D.iA0 = m->upload(iA0, err);
+    D.iq2 = m->upload(iq2, err);
+  }
   D.D = m->upload(T.D, err);
   D.R = m->upload(T.R, err);
   D.wt = m->upload(T.wt, err);

@@ -53,6 +53,8 @@ struct DevTables {
   int predictor;       // 0: one thread per zone; 1: a team of N threads per zone (one per node)
   int* status;         // [1] bit 0 set by the U update when a zone leaves rho > 0, p > 0 (or is not finite)
   const double* qpow;  // [nr + 2]: q^k
+  const double* iA0;   // [ncol][6]: 1 / A0 (reciprocal face areas at shell 0)
+  const double* iq2;   // [nr + 2]: q^-2k
   const double *D, *R, *wt, *psiF, *psiE, *wE;
   const int* st_n;
   const int* st_nb;

@@ -655,7 +655,6 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
     const long long z = zbase + zl;
     if (z >= Z) continue;
     const int c = static_cast<int>(z / nr), k = static_cast<int>(z % nr);
-    const double s1 = T.qpow[k];
     long long f;
     int sg, se = -1;
     if (lf < 4) {
@@ -673,8 +672,8 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
       const int ql = (lf < 4 && sg < 0) ? T.se_perm[se * Dm::NQS + q] : q;
       S.in[zl][3 * NC + foff<P>(lf) + ql] = rsg * Bp[static_cast<size_t>(q) * F + f];
     }
-    const double s2 = s1 * s1;
-    S.in[zl][3 * NC + NQT + lf] = static_cast<R>(sg * phi[f] / (T.A0[6 * c + lf] * s2));
+    // face mean <B_perp> = Phi / A with the tabulated reciprocal area (no FP64 division)
+    S.in[zl][3 * NC + NQT + lf] = static_cast<R>(sg * phi[f] * T.iA0[6 * c + lf] * T.iq2[k]);
   }
   __syncthreads();
   // ---- zone-mean B (Sec. IV.b step 10)
@@ -1021,30 +1020,45 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
     double wt = T.wt[m - 1];
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
-      R st[4][8];
-      for (int j = 0; j < nz; ++j) {
-        int sl = revs[j] ? NS - 1 - s : s;
-        const R* src = trE + trE_at<P>(zs[j], m, les[j] * NS + sl, Z);
+      // primitive state of each zone at the point, 1/rho formed once per zone
+      // (register arrays: every index below is static or goes through sel4)
+      R ir[4], vx[4], vy[4], vz[4], pr[4], bx[4], by[4], bz[4];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) st[j][v] = src[v * Z];
+      for (int j = 0; j < 4; ++j) {
+        R u[8] = {R(1), R(0), R(0), R(0), R(1), R(0), R(0), R(0)};
+        if (j < nz) {
+          const int sl = revs[j] ? NS - 1 - s : s;
+          const R* src = trE + trE_at<P>(zs[j], m, les[j] * NS + sl, Z);
+#pragma unroll
+          for (int v = 0; v < 8; ++v) u[v] = src[v * Z];
+        }
+        const Prim<R> w = to_prim(u, g);
+        ir[j] = R(1) / u[0];
+        vx[j] = w.vx; vy[j] = w.vy; vz[j] = w.vz; pr[j] = w.p;
+        bx[j] = w.bx; by[j] = w.by; bz[j] = w.bz;
       }
       R tx = static_cast<R>(tv[s][0]), ty = static_cast<R>(tv[s][1]), tz = static_cast<R>(tv[s][2]);
       R E = R(0);
-      for (int j = 0; j < nz; ++j) {
-        R ir = R(1) / st[j][0];
-        R vx = st[j][1] * ir, vy = st[j][2] * ir, vz = st[j][3] * ir;
-        R bx = st[j][5], by = st[j][6], bz = st[j][7];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
         // (-v x B) . t
-        E -= (vy * bz - vz * by) * tx + (vz * bx - vx * bz) * ty + (vx * by - vy * bx) * tz;
+        if (j < nz)
+          E -= (vy[j] * bz[j] - vz[j] * by[j]) * tx + (vz[j] * bx[j] - vx[j] * bz[j]) * ty +
+               (vx[j] * by[j] - vy[j] * bx[j]) * tz;
       }
-      for (int j = 0; j < nf; ++j) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= nf) continue;
         const double* nvd = fn[j] + 3 * s;
         R nx = static_cast<R>(nvd[0]), ny = static_cast<R>(nvd[1]), nzz = static_cast<R>(nvd[2]);
-        R a = fmax(rusanov_speed(st[fL[j]], nx, ny, nzz, g), rusanov_speed(st[fR[j]], nx, ny, nzz, g));
+        const int qL = fL[j], qR = fR[j];
+        R a = fmax(rusanov_speed_ir(sel4(ir, qL), sel4(vx, qL), sel4(vy, qL), sel4(vz, qL), sel4(pr, qL),
+                                    sel4(bx, qL), sel4(by, qL), sel4(bz, qL), nx, ny, nzz, g),
+                   rusanov_speed_ir(sel4(ir, qR), sel4(vx, qR), sel4(vy, qR), sel4(vz, qR), sel4(pr, qR),
+                                    sel4(bx, qR), sel4(by, qR), sel4(bz, qR), nx, ny, nzz, g));
         // t x n
         R cx = ty * nzz - tz * ny, cy = tz * nx - tx * nzz, cz = tx * ny - ty * nx;
-        R dbx = st[fR[j]][5] - st[fL[j]][5], dby = st[fR[j]][6] - st[fL[j]][6],
-          dbz = st[fR[j]][7] - st[fL[j]][7];
+        R dbx = sel4(bx, qR) - sel4(bx, qL), dby = sel4(by, qR) - sel4(by, qL), dbz = sel4(bz, qR) - sel4(bz, qL);
         E += a * (dbx * cx + dby * cy + dbz * cz);
       }
       acc += wt * dlw[s] * static_cast<double>(E * inz);

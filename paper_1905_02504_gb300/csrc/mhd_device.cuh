@@ -99,6 +99,24 @@ __device__ __forceinline__ R rusanov_speed(const R* u, R nx, R ny, R nz, R g) {
   return fabs(w.vx * nx + w.vy * ny + w.vz * nz) + fast_speed(w, nx, ny, nz, g);
 }
 
+// the same Rusanov speed from a primitive state whose 1/rho is already formed
+template <typename R>
+__device__ __forceinline__ R rusanov_speed_ir(R ir, R vx, R vy, R vz, R p, R bx, R by, R bz, R nx, R ny, R nz,
+                                              R g) {
+  R a2 = g * p * ir;
+  R b2 = (bx * bx + by * by + bz * bz) * ir;
+  R bn = bx * nx + by * ny + bz * nz;
+  R bn2 = bn * bn * ir;
+  R s = a2 + b2;
+  return fabs(vx * nx + vy * ny + vz * nz) + sqrt(R(0.5) * (s + sqrt(fmax(s * s - R(4) * a2 * bn2, R(0)))));
+}
+
+// a[q] for a runtime q in 0..3 of a register array (selects, no local memory)
+template <typename T>
+__device__ __forceinline__ T sel4(const T (&a)[4], int q) {
+  return q == 0 ? a[0] : (q == 1 ? a[1] : (q == 2 ? a[2] : a[3]));
+}
+
 template <typename R>
 __device__ __forceinline__ R minmod(R a, R b) {
   if (a * b > R(0)) return (a > R(0) ? R(1) : R(-1)) * fmin(fabs(a), fabs(b));
