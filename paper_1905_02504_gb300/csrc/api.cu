@@ -281,6 +281,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   S.Ff = m->alloc(8 * F, err);
   S.Ee = m->alloc(E, err);
   S.red = m->alloc(4096, err);
+  S.Uhl = f32 ? static_cast<float*>(m->alloc_bytes(sizeof(float) * 16 * Z, err)) : nullptr;
   m->dt.status = static_cast<int*>(m->alloc_bytes(sizeof(int), err));
   if (err == cudaSuccess) err = cudaMemset(m->dt.status, 0, sizeof(int));
   if (err == cudaSuccess) err = cudaMallocHost(&m->status_host, sizeof(int));
@@ -372,6 +373,7 @@ int geo_state_upload(geo_mesh_t m, const double* U, const double* phi, int on_de
   cudaError_t e = cudaMemcpyAsync(m->ds.U, U, 8 * m->T.Z * sizeof(double), kind, m->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->ds.phi, phi, m->T.F * sizeof(double), kind, m->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->dt.status, 0, sizeof(int), m->st);
+  if (e == cudaSuccess) e = geo::launch_split_u(m->dt, m->ds, m->st);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(m->st);
   if (e != cudaSuccess) return cuda_fail(e, "state upload");
   m->status_pending = false;

@@ -82,6 +82,7 @@ struct DevState {
   double* Ff;    // [8][F] time-integrated face fluxes (FP64 accumulation)
   double* Ee;    // [E]   time-integrated edge EMFs (FP64 accumulation)
   double* red;   // reduction scratch
+  float* Uhl;    // FP32-bulk only: [16][Z] U split as hi = fl(U), lo = fl(U - hi), for the WENO differences
 };
 
 // Work arrays of the adjoint step (FP64): cotangents of every forward quantity.
@@ -113,6 +114,8 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
 cudaError_t launch_cfl(const DevTables& T, const DevState& S, double cfl, double* out_host,
                        cudaStream_t st);
 cudaError_t launch_divb(const DevTables& T, const DevState& S, double* out2_host, cudaStream_t st);
+// refresh S.Uhl from S.U (FP32-bulk meshes, after an upload)
+cudaError_t launch_split_u(const DevTables& T, const DevState& S, cudaStream_t st);
 cudaError_t probe_fma(int prec, cudaStream_t st, double* flops_per_s);
 // reverse sweep of one step (FP64); the forward intermediates of the checkpoint
 // state are in S (Wc, Bp, trF, trE), the pristine checkpoint in A.U0

@@ -49,7 +49,7 @@ using namespace dev;
 // ----------------------------------------------------------------------------
 template <int P, typename R>
 __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* __restrict__ U,
-                                              R* __restrict__ Wc) {
+                                              const float* __restrict__ Uhl, R* __restrict__ Wc) {
   using Dm = Dim<P>;
   constexpr int NC1 = Dm::NC1, SMAX = Dm::SMAX;
   const R GH = R(0.85), GK = R(0.15 / 8.0), EPS = R(1e-12);
@@ -81,13 +81,22 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
   {
     const int v = blockIdx.y;  // one conserved variable per grid row
     const double* Uv = U + v * Z;
-    const double u0d = Uv[z];
-    const R u0 = static_cast<R>(u0d);
+    // zone-average differences U_j - U_0: in FP64 for the FP64 form; in the
+    // FP32-bulk form from the hi/lo split, (hi_j - hi_0) + (lo_j - lo_0), which
+    // carries the FP64 difference to FP32 rounding without FP64 arithmetic
+    const float* Hv = Uhl ? Uhl + static_cast<size_t>(v) * Z : nullptr;
+    const float* Lv = Uhl ? Uhl + static_cast<size_t>(8 + v) * Z : nullptr;
+    const double u0d = (sizeof(R) == 8) ? Uv[z] : 0.0;
+    const float h0 = (sizeof(R) == 4) ? Hv[z] : 0.f, l0 = (sizeof(R) == 4) ? Lv[z] : 0.f;
+    auto diff = [&](long long zz) -> R {
+      if constexpr (sizeof(R) == 4) return (Hv[zz] - h0) + (Lv[zz] - l0);
+      else return static_cast<R>(Uv[zz] - u0d);
+    };
     R uH[NC1];
 #pragma unroll
     for (int m = 0; m < NC1; ++m) uH[m] = R(0);
     for (int j = 0; j < ns; ++j) {
-      R du = static_cast<R>(Uv[zs[j]] - u0d);
+      R du = diff(zs[j]);
 #pragma unroll
       for (int m = 0; m < NC1; ++m) uH[m] += pinv[m * SMAX + j] * du;
     }
@@ -103,8 +112,7 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
     R tau = R(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      R d0 = static_cast<R>(Uv[zo[3 * o]] - u0d), d1 = static_cast<R>(Uv[zo[3 * o + 1]] - u0d),
-        d2 = static_cast<R>(Uv[zo[3 * o + 2]] - u0d);
+      R d0 = diff(zo[3 * o]), d1 = diff(zo[3 * o + 1]), d2 = diff(zo[3 * o + 2]);
       const R* A = oinv + 9 * o;
 #pragma unroll
       for (int a = 0; a < 3; ++a) uK[o][a] = A[3 * a] * d0 + A[3 * a + 1] * d1 + A[3 * a + 2] * d2;
@@ -138,7 +146,6 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
     }
 #pragma unroll
     for (int m = 3; m < NC1; ++m) out[m * Z + z] = fH * uH[m];
-    (void)u0;
   }
 }
 
@@ -558,7 +565,7 @@ __device__ __forceinline__ void smem_min_nonneg(double* a, double v) {
 // X is the zone's exchange buffer, chunk (alpha * NCH + c) * N + node
 template <int P, typename R>
 __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, const R* g, const R* Sa, R gam,
-                                                     R (*X)[Chunk<R>::CH], const R* Ev, const unsigned char* Ec,
+                                                     R (*X)[Chunk<R>::CH], const R* Ev, const unsigned* Ecr,
                                                      int i, bool valid) {
   using Dm = Dim<P>;
   constexpr int N = Dm::N, RL = Dm::RL, CH = Chunk<R>::CH, NCH = Chunk<R>::NCH;
@@ -587,7 +594,8 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
       for (int sl = 0; sl < RL; ++sl) {
         const R d = Ev[(al * RL + sl) * N + i];
         if (d != R(0)) {  // padding entries of short rows: no shared-memory traffic
-          const int j = Ec[(al * RL + sl) * N + i];
+          // this thread's column indices, four per register (static shifts)
+          const int j = (Ecr[(al * RL + sl) / 4] >> (8 * ((al * RL + sl) % 4))) & 0xff;
 #pragma unroll
           for (int c = 0; c < NCH; ++c) {
             R f[CH];
@@ -762,8 +770,16 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
   const R fs = S.fs[zl];
   constexpr int CH = Chunk<R>::CH, NCH = Chunk<R>::NCH;
   R (*X)[CH] = S.X[zl];
+  // the node's row of every D^alpha: values stay in shared memory, the column
+  // indices are packed into registers once
+  constexpr int NEC = (3 * Dm::RL + 3) / 4;
+  unsigned Ecr[NEC];
+#pragma unroll
+  for (int t = 0; t < NEC; ++t) Ecr[t] = 0u;
+#pragma unroll
+  for (int t = 0; t < 3 * Dm::RL; ++t) Ecr[t / 4] |= static_cast<unsigned>(S.Ec[t * N + i]) << (8 * (t % 4));
   R dF[M][8];
-  team_flux_difference<P, R>(Uh[0], dF[0], iJ, g, Sa, gam, X, S.Ev, S.Ec, i, valid);
+  team_flux_difference<P, R>(Uh[0], dF[0], iJ, g, Sa, gam, X, S.Ev, Ecr, i, valid);
 #pragma unroll
   for (int m = 1; m < M; ++m)
 #pragma unroll
@@ -772,7 +788,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
   for (int it = 0; it < P; ++it) {
     if (it > 0) {
 #pragma unroll
-      for (int m = 1; m < M; ++m) team_flux_difference<P, R>(Uh[m], dF[m], iJ, g, Sa, gam, X, S.Ev, S.Ec, i, valid);
+      for (int m = 1; m < M; ++m) team_flux_difference<P, R>(Uh[m], dF[m], iJ, g, Sa, gam, X, S.Ev, Ecr, i, valid);
     }
 #pragma unroll
     for (int kk = 1; kk < M; ++kk) {
@@ -1071,7 +1087,7 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
 // a6: conservative and constrained-transport updates
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(TPB) k_update_u(const DevTables T, double* __restrict__ U,
-                                                  const double* __restrict__ Ff) {
+                                                  const double* __restrict__ Ff, float* __restrict__ Uhl) {
   long long z = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (z >= T.Z) return;
   const long long Z = T.Z, F = T.F;
@@ -1102,10 +1118,29 @@ __global__ void __launch_bounds__(TPB) k_update_u(const DevTables T, double* __r
   for (int v = 0; v < 8; ++v) {
     u[v] = U[v * Z + z] - iV * acc[v];
     U[v * Z + z] = u[v];
+    if (Uhl) {
+      const float hi = static_cast<float>(u[v]);
+      Uhl[v * Z + z] = hi;
+      Uhl[(8 + v) * Z + z] = static_cast<float>(u[v] - static_cast<double>(hi));
+    }
   }
   // physical-state flag (read by the host between steps)
   const double p = pressure_of(u, T.gamma);
   if (!(u[0] > 0.0) || !(p > 0.0) || !isfinite(u[4])) atomicOr(T.status, 1);
+}
+
+__global__ void __launch_bounds__(TPB) k_split_u(const DevTables T, const double* __restrict__ U,
+                                                 float* __restrict__ Uhl) {
+  long long z = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (z >= T.Z) return;
+  const long long Z = T.Z;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const double u = U[v * Z + z];
+    const float hi = static_cast<float>(u);
+    Uhl[v * Z + z] = hi;
+    Uhl[(8 + v) * Z + z] = static_cast<float>(u - static_cast<double>(hi));
+  }
 }
 
 __global__ void __launch_bounds__(TPB) k_update_phi(const DevTables T, double* __restrict__ phi,
@@ -1353,7 +1388,7 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
   R* trE = static_cast<R*>(S.trE);
   switch (stage) {
     case ST_WENO:
-      k_weno<P, R><<<dim3(grid_for(T.Z), 8), TPB, 0, st>>>(T, S.U, Wc);
+      k_weno<P, R><<<dim3(grid_for(T.Z), 8), TPB, 0, st>>>(T, S.U, sizeof(R) == 4 ? S.Uhl : nullptr, Wc);
       break;
     case ST_BPERP:
       k_bperp<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp);
@@ -1380,7 +1415,7 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
       k_edge_emf<P, R><<<grid_for(T.E), TPB, 0, st>>>(T, trE, S.Ee, dt);
       break;
     case ST_UPD_U:
-      k_update_u<<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.Ff);
+      k_update_u<<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.Ff, S.Uhl);
       break;
     case ST_UPD_PHI:
       k_update_phi<<<grid_for(T.F), TPB, 0, st>>>(T, S.phi, S.Ee);
@@ -1419,6 +1454,12 @@ cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState
 template cudaError_t launch_adjoint<2>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
 template cudaError_t launch_adjoint<3>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
 template cudaError_t launch_adjoint<4>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
+
+cudaError_t launch_split_u(const DevTables& T, const DevState& S, cudaStream_t st) {
+  if (!S.Uhl) return cudaSuccess;
+  k_split_u<<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.Uhl);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_outer_br2(const DevTables& T, const double* phi, double* out_dev, double* gphi, cudaStream_t st) {
   k_outer_br2<<<1, 256, 0, st>>>(T, phi, out_dev, gphi);
