@@ -561,12 +561,16 @@ __device__ __forceinline__ void smem_min_nonneg(double* a, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
+// FP32 order 3 runs at its register limit for 4 blocks per SM: its column indices
+// stay in shared memory
+template <int P, typename R> struct EcInRegs { static constexpr bool value = !(P == 3 && sizeof(R) == 4); };
+
 // one flux difference of node i of a team: dF = sum_alpha sum_j D^alpha_ij F^alpha_j - F_i . g_i;
 // X is the zone's exchange buffer, chunk (alpha * NCH + c) * N + node
 template <int P, typename R>
 __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, const R* g, const R* Sa, R gam,
-                                                     R (*X)[Chunk<R>::CH], const R* Ev, const unsigned* Ecr,
-                                                     int i, bool valid) {
+                                                     R (*X)[Chunk<R>::CH], const R* Ev, const unsigned char* Ec,
+                                                     const unsigned* Ecr, int i, bool valid) {
   using Dm = Dim<P>;
   constexpr int N = Dm::N, RL = Dm::RL, CH = Chunk<R>::CH, NCH = Chunk<R>::NCH;
   if (valid) {
@@ -594,8 +598,10 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
       for (int sl = 0; sl < RL; ++sl) {
         const R d = Ev[(al * RL + sl) * N + i];
         if (d != R(0)) {  // padding entries of short rows: no shared-memory traffic
-          // this thread's column indices, four per register (static shifts)
-          const int j = (Ecr[(al * RL + sl) / 4] >> (8 * ((al * RL + sl) % 4))) & 0xff;
+          // column index: from registers (four per register, static shifts), or
+          // from shared memory where the registers are needed elsewhere
+          const int j = EcInRegs<P, R>::value ? (Ecr[(al * RL + sl) / 4] >> (8 * ((al * RL + sl) % 4))) & 0xff
+                                              : Ec[(al * RL + sl) * N + i];
 #pragma unroll
           for (int c = 0; c < NCH; ++c) {
             R f[CH];
@@ -776,10 +782,12 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
   unsigned Ecr[NEC];
 #pragma unroll
   for (int t = 0; t < NEC; ++t) Ecr[t] = 0u;
+  if constexpr (EcInRegs<P, R>::value) {
 #pragma unroll
-  for (int t = 0; t < 3 * Dm::RL; ++t) Ecr[t / 4] |= static_cast<unsigned>(S.Ec[t * N + i]) << (8 * (t % 4));
+    for (int t = 0; t < 3 * Dm::RL; ++t) Ecr[t / 4] |= static_cast<unsigned>(S.Ec[t * N + i]) << (8 * (t % 4));
+  }
   R dF[M][8];
-  team_flux_difference<P, R>(Uh[0], dF[0], iJ, g, Sa, gam, X, S.Ev, Ecr, i, valid);
+  team_flux_difference<P, R>(Uh[0], dF[0], iJ, g, Sa, gam, X, S.Ev, S.Ec, Ecr, i, valid);
 #pragma unroll
   for (int m = 1; m < M; ++m)
 #pragma unroll
@@ -788,7 +796,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
   for (int it = 0; it < P; ++it) {
     if (it > 0) {
 #pragma unroll
-      for (int m = 1; m < M; ++m) team_flux_difference<P, R>(Uh[m], dF[m], iJ, g, Sa, gam, X, S.Ev, Ecr, i, valid);
+      for (int m = 1; m < M; ++m) team_flux_difference<P, R>(Uh[m], dF[m], iJ, g, Sa, gam, X, S.Ev, S.Ec, Ecr, i, valid);
     }
 #pragma unroll
     for (int kk = 1; kk < M; ++kk) {
