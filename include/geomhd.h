@@ -173,7 +173,9 @@ int geo_divB_max(geo_mesh_t mesh, double* abs_max, double* rel_max);
  * pointers (caller-owned): U_in double[8][Z] and phi_in double[F] are the state
  * at t (the checkpoint; the step is recomputed from it), gU_out / gphi_out the
  * cotangent at t + dt; gU_in / gphi_in receive the cotangent at t.  Only for
- * GEO_FP64 meshes (GEO_ERR_ARG otherwise).  The mesh's own state is untouched;
+ * GEO_FP64 meshes with the positivity scaling off (GEO_ERR_ARG otherwise; the
+ * FP32-bulk form is differentiated by an FP64 mesh of the same geometry applied
+ * to its checkpoints).  The mesh's own state is untouched;
  * work buffers are allocated on the first call.  Asynchronous on the mesh stream. */
 int geo_step_adjoint(geo_mesh_t mesh, double dt, const double* U_in, const double* phi_in,
                      const double* gU_out, const double* gphi_out, double* gU_in, double* gphi_in);

@@ -3,7 +3,9 @@
 StepWindow runs K steps of fixed dt through the C ABI, keeping one checkpoint
 (U, phi) per step on the device; its backward walks the steps in reverse and
 calls geo_step_adjoint on each checkpoint (the step is recomputed inside the
-adjoint call).  OuterBr2 is J = sum over the outer radial faces of phi^2 / A.
+adjoint call).  For an FP32-bulk mesh the forward steps run in the FP32-bulk
+form and the reverse sweep on an FP64 mesh of the same geometry, i.e. the FP64
+linearisation of the step about the FP32-bulk trajectory.  OuterBr2 is J = sum over the outer radial faces of phi^2 / A.
 Both compute only in the CUDA library; torch provides the tensors.
 """
 import torch
@@ -32,10 +34,11 @@ class StepWindow(torch.autograd.Function):
     def backward(ctx, gU, gphi):
         gU = (torch.zeros_like(ctx.checkpoints[0][0]) if gU is None else gU).contiguous()
         gphi = (torch.zeros_like(ctx.checkpoints[0][1]) if gphi is None else gphi).contiguous()
+        adj = ctx.mesh.adjoint_mesh()
         for U_s, phi_s in reversed(ctx.checkpoints):
             gU_in = torch.empty_like(gU)
             gphi_in = torch.empty_like(gphi)
-            geomhd.geo_step_adjoint(ctx.mesh.h, ctx.dt, U_s, phi_s, gU, gphi, gU_in, gphi_in)
+            geomhd.geo_step_adjoint(adj.h, ctx.dt, U_s, phi_s, gU, gphi, gU_in, gphi_in)
             gU, gphi = gU_in, gphi_in
         torch.cuda.current_stream().synchronize()
         return gU, gphi, None, None, None

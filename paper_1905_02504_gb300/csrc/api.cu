@@ -581,6 +581,8 @@ int geo_step_adjoint(geo_mesh_t m, double dt, const double* U_in, const double* 
   if (!m || !U_in || !phi_in || !gU_out || !gphi_out || !gU_in || !gphi_in || !(dt > 0.0))
     return fail(GEO_ERR_ARG, "geo_step_adjoint: bad arguments");
   if (m->prec != GEO_FP64) return fail(GEO_ERR_ARG, "geo_step_adjoint: the adjoint is available for GEO_FP64 meshes");
+  if (m->dt.positivity)
+    return fail(GEO_ERR_ARG, "geo_step_adjoint: the positivity scaling is not differentiated; switch it off");
   int rc = ensure_adjoint_buffers(m);
   if (rc != GEO_OK) return rc;
   const size_t Z = m->T.Z, F = m->T.F;

@@ -272,10 +272,29 @@ class Mesh:
         self.h = geo_mesh_create(subdiv, nr, r_in, r_out, order, prec, stream)
         self.Z, self.F, self.E = geo_mesh_sizes(self.h)
         self.order = order
+        self.prec = prec
+        self.args = (subdiv, nr, r_in, r_out, order)
+        self.stream = stream
+        self.gamma = gamma
+        self._adjoint_twin = None
         if gamma != 5.0 / 3.0:
             geo_set_gamma(self.h, gamma)
 
+    def adjoint_mesh(self):
+        """The mesh whose geo_step_adjoint differentiates this mesh's steps: itself
+        for the FP64 form; for the FP32-bulk form an FP64 mesh of the same geometry
+        (made on first use), which linearises the step about the FP32-bulk
+        checkpoints."""
+        if self.prec == GEO_FP64:
+            return self
+        if self._adjoint_twin is None:
+            self._adjoint_twin = Mesh(*self.args, prec=GEO_FP64, stream=self.stream, gamma=self.gamma)
+        return self._adjoint_twin
+
     def close(self):
+        if self._adjoint_twin is not None:
+            self._adjoint_twin.close()
+            self._adjoint_twin = None
         if self.h:
             geo_mesh_destroy(self.h)
             self.h = None

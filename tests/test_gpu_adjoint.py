@@ -225,3 +225,35 @@ def test_window_objective_gradient_with_checkpoints():
         checked += 1
     assert checked >= 4
     mesh.close()
+
+
+def test_fp32_bulk_window_gradient_matches_fp64():
+    """The FP32-bulk form is differentiated by the FP64 adjoint applied to its own
+    (FP32-bulk) checkpoints.  Its window gradient agrees with the FP64 form's to
+    the FP32-bulk state error (directional derivatives within 1e-4 relative), and
+    differs from it (the checkpoints really are the FP32-bulk ones)."""
+    import torch
+    from paper_1905_02504_gb300 import autodiff, geomhd
+    K = 3
+    o, m64, U, phi = setup_case(3, 3, 3)
+    U, _ = clean_base_state(o, U, phi, 3, K=K, margin=5e-7)
+    dt = o.cfl_dt(U, 0.4)
+    m32 = geomhd.Mesh(3, 3, 1.0, 2.0, 3, prec=geomhd.GEO_FP32_BULK)
+    grads = []
+    for mesh in (m64, m32):
+        Ut = torch.from_numpy(np.ascontiguousarray(U.T)).cuda().requires_grad_(True)
+        pt = torch.from_numpy(phi.copy()).cuda().requires_grad_(True)
+        _, pK = autodiff.step_window(mesh, Ut, pt, dt, K)
+        autodiff.outer_br2(mesh, pK).backward()
+        grads.append((Ut.grad.cpu().numpy().T, pt.grad.cpu().numpy()))
+    rng = np.random.default_rng(32)
+    worst, differs = 0.0, False
+    for _ in range(4):
+        dU, dphi = direction(o, U, rng)
+        d64 = (grads[0][0] * dU).sum() + (grads[0][1] * dphi).sum()
+        d32 = (grads[1][0] * dU).sum() + (grads[1][1] * dphi).sum()
+        worst = max(worst, abs(d32 - d64) / abs(d64))
+        differs = differs or d32 != d64
+    assert worst < 1e-4 and differs, worst
+    m32.close()
+    m64.close()
