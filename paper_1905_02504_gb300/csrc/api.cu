@@ -243,8 +243,10 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.sv_t = m->upload(T.sv_t, err);
   D.sv_dlw = m->upload(T.sv_dlw, err);
   // bulk-arithmetic views of the per-column matrices
-  D.b64 = geo::BulkTables<double>{D.pinvH, D.oct_inv, D.Q, D.TF, D.nF, D.wF, D.GB, D.TN, D.J0, D.iJ0,
-                                  D.Sm, D.gcl, D.JF, D.JE};
+  D.b64 = geo::BulkTables<double>{D.pinvH, D.oct_inv, D.Q,        D.TF,       D.nF,       D.wF,
+                                  D.GB,    D.TN,      D.J0,       D.iJ0,      D.Sm,       D.gcl,
+                                  D.JF,    D.JE,      D.se_t,     D.se_nang,  D.se_nradL, D.se_nradR,
+                                  D.sv_fn, D.sv_t};
   const bool f32 = prec == GEO_FP32_BULK;
   if (f32) {
     geo::BulkTables<float>& b = D.b32;
@@ -262,6 +264,12 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
     b.gcl = m->upload_f32(T.gcl, err);
     b.JF = m->upload_f32(T.JF, err);
     b.JE = m->upload_f32(T.JE, err);
+    b.se_t = m->upload_f32(T.se_t, err);
+    b.se_nang = m->upload_f32(T.se_nang, err);
+    b.se_nradL = m->upload_f32(T.se_nradL, err);
+    b.se_nradR = m->upload_f32(T.se_nradR, err);
+    b.sv_fn = m->upload_f32(T.sv_fn, err);
+    b.sv_t = m->upload_f32(T.sv_t, err);
   }
   if (err == cudaSuccess) {
     if (order == 2) err = f32 ? geo::upload_reference_constants<2, float>(T) : geo::upload_reference_constants<2, double>(T);

@@ -42,6 +42,8 @@ template <int P, typename R> struct RefConst {
 // threads of a node team read consecutive entries.
 template <typename R> struct BulkTables {
   const R *pinvH, *oct_inv, *Q, *TF, *nF, *wF, *GB, *TN, *J0, *iJ0, *Sm, *gcl, *JF, *JE;
+  // edge geometry: unit tangents and face normals at the edge points
+  const R *se_t, *se_nang, *se_nradL, *se_nradR, *sv_fn, *sv_t;
 };
 
 // Read-only tables in device memory (see host_tables.h for the layouts).

@@ -164,12 +164,19 @@ __global__ void __launch_bounds__(TPB) k_bperp(const DevTables T, const double* 
   const long long Z = T.Z, F = T.F;
   FaceInfo fi = face_info(T, f);
   int nq = nq_of<P>(fi.lfg);
-  double s2 = T.qpow[fi.k] * T.qpow[fi.k];
-  double area = T.A0[6 * fi.cg + fi.lfg] * s2;
-  const R mean = static_cast<R>(phi[f] / area);
+  // face mean <B_perp> = Phi / A with the tabulated reciprocal area
+  const R mean = static_cast<R>(phi[f] * T.iA0[6 * fi.cg + fi.lfg] * T.iq2[fi.k]);
   const R gs = static_cast<R>(fi.gsign);
   int cL = fi.zL >= 0 ? static_cast<int>(fi.zL / T.nr) : -1;
   int cR = fi.zR >= 0 ? static_cast<int>(fi.zR / T.nr) : -1;
+  // zone-mean B of both sides, converted once
+  R UB[2][3];
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const long long zz = sd == 0 ? fi.zL : fi.zR;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) UB[sd][d] = zz >= 0 ? static_cast<R>(U[(5 + d) * Z + zz]) : R(0);
+  }
   R b[NQMAX];
   R wsum = R(0);
   for (int q = 0; q < nq; ++q) {
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(TPB) k_bperp(const DevTables T, const double* 
       R Bv[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        R s = static_cast<R>(U[(5 + d) * Z + zz]);
+        R s = UB[sd][d];
 #pragma unroll
         for (int m = 0; m < NC1; ++m) s += tf[m] * Wc[((5 + d) * NC1 + m) * Z + zz];
         Bv[d] = s;
@@ -930,9 +937,11 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* _
   double s2 = T.qpow[fi.k] * T.qpow[fi.k];
   const R gs = static_cast<R>(fi.gsign);
   const R g = static_cast<R>(T.gamma);
-  double acc[8];
+  // quadrature sum over the face's points and Gauss times in the bulk type (the
+  // zone update that sums the faces is FP64)
+  R acc[8];
 #pragma unroll
-  for (int v = 0; v < 8; ++v) acc[v] = 0.0;
+  for (int v = 0; v < 8; ++v) acc[v] = R(0);
 #pragma unroll 1
   for (int m = 1; m < M; ++m) {
     double wt = T.wt[m - 1];
@@ -941,7 +950,7 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* _
       int ig = foff<P>(fi.lfg) + q;
       const R* nv = BT.nF + (static_cast<size_t>(fi.cg) * NQT + ig) * 3;
       R nx = gs * nv[0], ny = gs * nv[1], nz = gs * nv[2];
-      double W = wt * T.WF[static_cast<size_t>(fi.cg) * NQT + ig] * s2;
+      const R W = static_cast<R>(wt * T.WF[static_cast<size_t>(fi.cg) * NQT + ig] * s2);
       R uL[8], uR[8];
       if (fi.zL >= 0) {
         const R* src = trF + trF_at<P>(fi.zL, m, foff<P>(fi.lfL) + q, Z);
@@ -967,7 +976,7 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* _
     }
   }
 #pragma unroll
-  for (int v = 0; v < 8; ++v) Ff[v * F + f] = dt * acc[v];
+  for (int v = 0; v < 8; ++v) Ff[v * F + f] = dt * static_cast<double>(acc[v]);
 }
 
 // ----------------------------------------------------------------------------
@@ -988,8 +997,9 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
   int les[4], revs[4];
   int nz = 0, nf = 0;
   int fL[4], fR[4];
-  const double* fn[4];  // normals [NS][3] of each face
-  double tv[NS][3], dlw[NS];
+  const BulkTables<R>& BT = bulk<R>(T);
+  const R* fn[4];  // normals [NS][3] of each face
+  R tv[NS][3], dlw[NS];
   if (e < T.E_rad) {
     int sv = static_cast<int>(e / nr), k = static_cast<int>(e % nr);
     nz = T.sv_nc[sv];
@@ -1000,18 +1010,18 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
       revs[j] = 0;
       fL[j] = T.sv_fL[4 * sv + j];
       fR[j] = T.sv_fR[4 * sv + j];
-      fn[j] = T.sv_fn + static_cast<size_t>(sv * 4 + j) * NS * 3;
+      fn[j] = BT.sv_fn + static_cast<size_t>(sv * 4 + j) * NS * 3;
     }
     for (int s = 0; s < NS; ++s) {
-      for (int a = 0; a < 3; ++a) tv[s][a] = T.sv_t[3 * sv + a];
-      dlw[s] = T.sv_dlw[sv * NS + s] * T.qpow[k];
+      for (int a = 0; a < 3; ++a) tv[s][a] = BT.sv_t[3 * sv + a];
+      dlw[s] = static_cast<R>(T.sv_dlw[sv * NS + s] * T.qpow[k]);
     }
   } else {
     long long r = e - T.E_rad;
     int se = static_cast<int>(r / (nr + 1)), kk = static_cast<int>(r % (nr + 1));
     int cL = T.se_col[2 * se], cR = T.se_col[2 * se + 1];
     int revL = T.se_rev[2 * se], revR = T.se_rev[2 * se + 1];
-    const double* nang = T.se_nang + static_cast<size_t>(se) * NS * 3;
+    const R* nang = BT.se_nang + static_cast<size_t>(se) * NS * 3;
     if (kk >= 1 && kk <= nr - 1) {
       nz = 4;
       zs[0] = static_cast<long long>(cL) * nr + kk - 1; les[0] = T.se_le[(2 * se) * 2 + 1]; revs[0] = revL;
@@ -1021,8 +1031,8 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
       nf = 4;
       fL[0] = 0; fR[0] = 2; fn[0] = nang;
       fL[1] = 1; fR[1] = 3; fn[1] = nang;
-      fL[2] = 0; fR[2] = 1; fn[2] = T.se_nradL + static_cast<size_t>(se) * NS * 3;
-      fL[3] = 2; fR[3] = 3; fn[3] = T.se_nradR + static_cast<size_t>(se) * NS * 3;
+      fL[2] = 0; fR[2] = 1; fn[2] = BT.se_nradL + static_cast<size_t>(se) * NS * 3;
+      fL[3] = 2; fR[3] = 3; fn[3] = BT.se_nradR + static_cast<size_t>(se) * NS * 3;
     } else {
       nz = 2;
       int top = (kk == nr) ? 1 : 0;
@@ -1033,15 +1043,15 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
       fL[0] = 0; fR[0] = 1; fn[0] = nang;
     }
     for (int s = 0; s < NS; ++s) {
-      for (int a = 0; a < 3; ++a) tv[s][a] = T.se_t[(static_cast<size_t>(se) * NS + s) * 3 + a];
-      dlw[s] = T.se_dlw[se * NS + s] * T.qpow[kk];
+      for (int a = 0; a < 3; ++a) tv[s][a] = BT.se_t[(static_cast<size_t>(se) * NS + s) * 3 + a];
+      dlw[s] = static_cast<R>(T.se_dlw[se * NS + s] * T.qpow[kk]);
     }
   }
   const R inz = R(1) / static_cast<R>(nz);
-  double acc = 0.0;
+  R acc = R(0);  // quadrature sum in the bulk type; the Phi update is FP64
 #pragma unroll 1
   for (int m = 1; m < M; ++m) {
-    double wt = T.wt[m - 1];
+    const R wt = static_cast<R>(T.wt[m - 1]);
 #pragma unroll 1
     for (int s = 0; s < NS; ++s) {
       // primitive state of each zone at the point, 1/rho formed once per zone
@@ -1061,7 +1071,7 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
         vx[j] = w.vx; vy[j] = w.vy; vz[j] = w.vz; pr[j] = w.p;
         bx[j] = w.bx; by[j] = w.by; bz[j] = w.bz;
       }
-      R tx = static_cast<R>(tv[s][0]), ty = static_cast<R>(tv[s][1]), tz = static_cast<R>(tv[s][2]);
+      R tx = tv[s][0], ty = tv[s][1], tz = tv[s][2];
       R E = R(0);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -1073,8 +1083,8 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (j >= nf) continue;
-        const double* nvd = fn[j] + 3 * s;
-        R nx = static_cast<R>(nvd[0]), ny = static_cast<R>(nvd[1]), nzz = static_cast<R>(nvd[2]);
+        const R* nvd = fn[j] + 3 * s;
+        R nx = nvd[0], ny = nvd[1], nzz = nvd[2];
         const int qL = fL[j], qR = fR[j];
         R a = fmax(rusanov_speed_ir(sel4(ir, qL), sel4(vx, qL), sel4(vy, qL), sel4(vz, qL), sel4(pr, qL),
                                     sel4(bx, qL), sel4(by, qL), sel4(bz, qL), nx, ny, nzz, g),
@@ -1085,10 +1095,10 @@ __global__ void __launch_bounds__(TPB) k_edge_emf(const DevTables T, const R* __
         R dbx = sel4(bx, qR) - sel4(bx, qL), dby = sel4(by, qR) - sel4(by, qL), dbz = sel4(bz, qR) - sel4(bz, qL);
         E += a * (dbx * cx + dby * cy + dbz * cz);
       }
-      acc += wt * dlw[s] * static_cast<double>(E * inz);
+      acc += wt * dlw[s] * (E * inz);
     }
   }
-  Ee[e] = dt * acc;
+  Ee[e] = dt * static_cast<double>(acc);
 }
 
 // ----------------------------------------------------------------------------

@@ -66,10 +66,9 @@ __device__ __forceinline__ R fast_speed(const Prim<R>& w, R nx, R ny, R nz, R g)
 }
 
 // HLL flux along the unit normal (Davis wave speeds); the weighted flux is
-// accumulated in FP64
-template <typename R>
-__device__ __forceinline__ void hll_acc(const R* uL, const R* uR, R nx, R ny, R nz, R g, double w,
-                                        double* acc) {
+// accumulated in the type A
+template <typename R, typename A>
+__device__ __forceinline__ void hll_acc(const R* uL, const R* uR, R nx, R ny, R nz, R g, A w, A* acc) {
   Prim<R> a = to_prim(uL, g), b = to_prim(uR, g);
   R vnL = a.vx * nx + a.vy * ny + a.vz * nz;
   R vnR = b.vx * nx + b.vy * ny + b.vz * nz;
@@ -81,15 +80,15 @@ __device__ __forceinline__ void hll_acc(const R* uL, const R* uR, R nx, R ny, R 
   flux_n(uR, b, nx, ny, nz, FR);
   if (SL >= R(0)) {
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FL[v]);
+    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<A>(FL[v]);
   } else if (SR <= R(0)) {
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<double>(FR[v]);
+    for (int v = 0; v < 8; ++v) acc[v] += w * static_cast<A>(FR[v]);
   } else {
     R id = R(1) / (SR - SL);
 #pragma unroll
     for (int v = 0; v < 8; ++v)
-      acc[v] += w * static_cast<double>((SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * id);
+      acc[v] += w * static_cast<A>((SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * id);
   }
 }
 
