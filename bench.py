@@ -81,6 +81,14 @@ def workload_name(a):
         6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order, form, getattr(a, "problem", "smooth"), extra)
 
 
+def kernel_name(stage, pred):
+    """Name of the kernel that runs a stage (the predictor stage has two schedules)."""
+    name = "k_" + stage
+    if stage == "ader" and (pred is None or pred == 1):
+        name += "_team"
+    return name
+
+
 def sched_name(pred, fp32):
     """Predictor schedule in use (the library default is the node team)."""
     if pred is None:
@@ -311,7 +319,7 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": achieved / nominal_fp32,
                      "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], m32.Z, "fp32"),
-                     "kernel": "k_" + geomhd.STAGES[top],
+                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor),
                      "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
                                   "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
                      "measured_fp32_fma_tflops": fp32_probe},
@@ -425,7 +433,7 @@ def gpu_arm(a):
     roofline = {"bound": "alu", "achieved": achieved, "peak": nominal, "unit": "TFLOP/s",
                 "frac": achieved / nominal,
                 "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], Z, "fp32" if a.fp32_only else "fp64"),
-                "kernel": "k_" + geomhd.STAGES[top], "peak_kind": kind, "measured_fma_tflops": fma_peak}
+                "kernel": kernel_name(geomhd.STAGES[top], a.predictor), "peak_kind": kind, "measured_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
     fp32 = None if (a.no_fp32 or a.fp32_only) else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
