@@ -625,7 +625,7 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
 // resident blocks per SM the register budget is sized for
 template <int P, typename R> struct TeamOcc;
 template <> struct TeamOcc<2, float> { static constexpr int MINB = 8; };   // 128 threads
-template <> struct TeamOcc<3, float> { static constexpr int MINB = 4; };   // 160 threads
+template <> struct TeamOcc<3, float> { static constexpr int MINB = 5; };   // 160 threads (72 registers, a few spilled)
 template <> struct TeamOcc<4, float> { static constexpr int MINB = 4; };   // 128 threads (128 registers, a few spilled)
 template <> struct TeamOcc<2, double> { static constexpr int MINB = 4; };
 template <> struct TeamOcc<3, double> { static constexpr int MINB = 2; };
