@@ -568,7 +568,7 @@ __device__ __forceinline__ void smem_min_nonneg(double* a, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
-// FP32 order 3 runs at its register limit for 4 blocks per SM: its column indices
+// FP32 order 3 runs at its register limit (5 blocks per SM): its column indices
 // stay in shared memory
 template <int P, typename R> struct EcInRegs { static constexpr bool value = !(P == 3 && sizeof(R) == 4); };
 
