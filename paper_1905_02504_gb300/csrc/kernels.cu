@@ -552,7 +552,7 @@ struct TeamSmem {
   R Ev[3 * Dm::RL * Dm::N];
   R psiF[Dm::NQT * Dm::NFN];
   R psiE[12 * Dm::NS * Dm::NEN];
-  R th[ZB][4];                       // positivity factors (min-reduced)
+  R th[ZB][5];                       // positivity factors (min-reduced)
   R fs[ZB];                          // dt l_0 / l_k of the zone (Eq. 5.21)
   unsigned char Ec[3 * Dm::RL * Dm::N];
   unsigned char fnode[6 * Dm::NFN];
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
   for (int t = tid; t < 6 * Dm::NFN; t += NT) S.fnode[t] = K.fnode[t];
   for (int t = tid; t < 12 * NS * Dm::NEN; t += NT) S.psiE[t] = K.psiEc[t];
   for (int t = tid; t < 12 * Dm::NEN; t += NT) S.enode[t] = K.enode[t];
-  for (int w = tid; w < ZB * 4; w += NT) S.th[w / 4][w % 4] = R(1);
+  for (int w = tid; w < ZB * 5; w += NT) S.th[w / 5][w % 5] = R(1);
   for (int w = tid; w < ZB * 3 * NC; w += NT) {
     const int zl = w % ZB, e = w / ZB, d = e / NC, t = e % NC;
     const long long z = zbase + zl;
@@ -837,8 +837,13 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
     const R* JE = BT.JE + static_cast<size_t>(c2) * 12 * NS;
     const R(*X2)[CH] = S.X[zl2];
     const R* Uz = S.Uz[zl2];
+    // with positivity: pass 0 writes the unscaled values and min-reduces theta_rho
+    // and the pressure factor for theta_rho = 1; pass 1 (only if some zone of the
+    // block has theta_rho < 1) recomputes the pressure factor of those zones; pass 2
+    // (only if some zone has theta < 1) rewrites those zones' values scaled
     constexpr int NPASS = POS ? 3 : 1;
     R pbar = R(0), eps_r = R(0), eps_p = R(0), th = R(1);
+    bool redo = true;  // this zone takes part in the current pass
     if constexpr (POS) {
       pbar = pressure_of(Uz, gam);
       eps_r = fmin(R(1e-13), Uz[0]);
@@ -847,10 +852,20 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
       if constexpr (POS) {
-        if (pass == 2) th = S.th[zl2][2] * S.th[zl2][3];
+        if (pass == 1) {
+          redo = valid2 && S.th[zl2][2] < R(1);
+          if (!__syncthreads_or(redo)) continue;  // block-uniform
+        }
+        if (pass == 2) {
+          const R thp = S.th[zl2][2] < R(1) ? S.th[zl2][3] : S.th[zl2][4];
+          th = S.th[zl2][2] * thp;
+          redo = valid2 && th < R(1);
+          if (!__syncthreads_or(redo)) continue;  // block-uniform
+        }
       }
 #pragma unroll 1
       for (int t = tid / ZB; t < NPT; t += N) {
+        if (!redo) break;
         R s[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) s[v] = R(0);
@@ -896,18 +911,17 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
         if (!valid2) continue;
         if constexpr (POS) {
           if (pass == 0) {
-            R th_r = R(1);
+            R th_r = R(1), th_p1 = R(1);
             pos_rho(s, Uz, eps_r, th_r);
             if (th_r < R(1)) smem_min_nonneg(&S.th[zl2][2], th_r);
-            continue;
-          }
-          if (pass == 1) {
+            pos_p(s, Uz, R(1), gam, pbar, eps_p, th_p1);
+            if (th_p1 < R(1)) smem_min_nonneg(&S.th[zl2][4], th_p1);
+          } else if (pass == 1) {
             R th_p = R(1);
             pos_p(s, Uz, S.th[zl2][2], gam, pbar, eps_p, th_p);
             if (th_p < R(1)) smem_min_nonneg(&S.th[zl2][3], th_p);
             continue;
-          }
-          if (th < R(1)) {
+          } else {
 #pragma unroll
             for (int v = 0; v < 8; ++v) s[v] = Uz[v] + th * (s[v] - Uz[v]);
           }
