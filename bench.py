@@ -96,6 +96,23 @@ def sched_name(pred, fp32):
     return "node-team" if pred == 1 else "zone-thread"
 
 
+def max_over_ranks(x, ws, device):
+    """The largest of the ranks' values of x (the slowest replica's time); x itself
+    for one rank."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_throughput(zones, steps, t_ms, ws):
+    """Whole-job zone-updates/s of ws independent replicas of `zones` zones that all
+    ran `steps` steps, the slowest taking t_ms."""
+    return ws * zones * steps / (t_ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -293,7 +310,7 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
             m32.step(dt)
             ev[i][1].record(stream)
     barrier()
-    t_ms = sum(s.elapsed_time(e) for s, e in ev)
+    t_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in ev), ws, "cuda")
     geomhd.geo_set_stage_timing(m32.h, 0)
     stage_ms, stage_cnt = geomhd.geo_get_stage_timing(m32.h)
     avg = stage_ms / np.maximum(stage_cnt, 1)
@@ -314,7 +331,7 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
     errp = float(np.abs(p32 - p64).sum() / np.abs(p64).sum())
     _, r32 = m32.divB()
     out = {
-        "value": ws * m32.Z * a.steps / (t_ms * 1e-3), "unit": "zone-updates/s",
+        "value": replica_throughput(m32.Z, a.steps, t_ms, ws), "unit": "zone-updates/s",
         "ms_per_step": t_ms / a.steps, "dtype": "f32 bulk / f64 accumulation and updates",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": achieved / nominal_fp32,
@@ -389,13 +406,9 @@ def gpu_arm(a):
     step_ms = [s.elapsed_time(e) for s, e in ev]
     geomhd.geo_set_stage_timing(mesh.h, 0)
     stage_ms, stage_cnt = geomhd.geo_get_stage_timing(mesh.h)
-    t_ms = sum(step_ms)
-    if ws > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = tt.item()
+    t_ms = max_over_ranks(sum(step_ms), ws, "cuda")
     Z = mesh.Z
-    value = ws * Z * a.steps / (t_ms * 1e-3)
+    value = replica_throughput(Z, a.steps, t_ms, ws)
     a_div, r_div = mesh.divB()
 
     # ---- end to end through the C ABI with pinned host buffers
