@@ -1,6 +1,7 @@
 // Device helpers shared by the forward kernels (kernels.cu) and the adjoint
-// kernels (adjoint.cu): ideal MHD fluxes in rationalised units (Eq. 2.2), the
-// HLL solver, the Rusanov speed, MinMod, and the face/zone index maps.
+// kernels (adjoint_kernels.inc): ideal MHD fluxes in rationalised units (Eq. 2.2),
+// the HLL solver, the Rusanov speed, MinMod, the positivity factors, and the
+// face/zone index maps.
 #pragma once
 #include "device.cuh"
 
@@ -131,10 +132,6 @@ __device__ __forceinline__ R pressure_of(const R* u, R g) {
   return (g - R(1)) * (u[4] - R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir -
                        R(0.5) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]));
 }
-
-struct PosAcc {
-  double th_r = 1.0, th_p = 1.0;
-};
 
 template <typename R>
 __device__ __forceinline__ void pos_rho(const R* s, const R* mean, R eps_r, R& th_r) {
