@@ -9,7 +9,7 @@ from oracle.step import Oracle
 from paper_1905_02504_gb300.inputs import make_problem
 
 
-@pytest.fixture(scope="module", params=[2, 3])
+@pytest.fixture(scope="module", params=[2, 3, 4])
 def orc(request):
     return Oracle(3, 3, 1.0, 2.0, request.param)
 
@@ -21,8 +21,11 @@ def test_free_stream_preserved(orc):
     U1, phi1 = U, phi
     for _ in range(2):
         U1, phi1 = orc.step(U1, phi1, dt)
-    assert (np.abs(U1 - U).max(0) / np.abs(U).max(0)).max() < 1e-14
-    assert np.abs(phi1 - phi).max() < 1e-14 * np.abs(phi).max()
+    # rounding only: order 4 performs several times the operations of order 2 per
+    # zone (32 nodes, 4 time levels, 10 flux evaluations), hence its wider bound
+    tol = 1e-14 if orc.mesh.p < 4 else 4e-14
+    assert (np.abs(U1 - U).max(0) / np.abs(U).max(0)).max() < tol
+    assert np.abs(phi1 - phi).max() < tol * np.abs(phi).max()
 
 
 def test_divb_and_conservation_ledger(orc):
