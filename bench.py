@@ -1,9 +1,12 @@
 """Throughput of the full ADER-WENO-CT step on one GB300 (zone-updates/s).
 
-Workload (default): cubed-sphere mesh 6 x 32 x 32 angular zones x 32 log shells
-in r in [1, 2] (196,608 zones), 3rd order, FP64, smooth test problem
+Workload (default): cubed-sphere mesh 6 x 64 x 64 angular zones x 64 log shells
+in r in [1, 2] (1,572,864 zones), 4th order, FP64, smooth test problem
 (rho = 1 + 0.1 sin(2 pi (x+y+z)/sqrt3), p = 1, v = (.5,.5,.5), B = curl of
-A = 0.1 (sin 2 pi z, sin 2 pi x, sin 2 pi y)), dt from CFL 0.4 of the initial state.
+A = 0.1 (sin 2 pi z, sin 2 pi x, sin 2 pi y)), dt from CFL 0.4 of the initial state;
+the FP32-bulk form of the same workload is timed beside it ("fp32_bulk"), and the
+6 x 32 x 32 x 32 (196,608 zones) 3rd-order smooth test in both forms as an extra
+key ("order3_196608").
 
 Timed region: K steps, each bracketed by CUDA events on the mesh stream, with an
 L2 flush (a 512 MB device write) between steps outside the events.  `value` is
@@ -36,9 +39,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=32)
-    ap.add_argument("--nr", type=int, default=32)
-    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--nr", type=int, default=64)
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra 196,608-zone order-3 measurement")
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
@@ -350,6 +355,43 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
     return out
 
 
+def extra_workload(a, stream, flush, barrier, ws, n=32, nr=32, order=3):
+    """The 6 x 32 x 32 x 32 (196,608 zones) order-3 smooth test, both forms, with the
+    same timed protocol (warm-up, L2 flush between steps, CUDA events on the mesh
+    stream): zone-updates/s and ms per step."""
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    from paper_1905_02504_gb300.inputs import make_problem
+    out = {"workload": "cubed-sphere 6x%dx%dx%d x %d shells (%d zones), order %d, smooth test" % (
+        n, n, n, nr, 6 * n * n * nr, order, )}
+    U0 = phi0 = dt = None
+    for key, prec in (("f64", geomhd.GEO_FP64), ("f32_bulk", geomhd.GEO_FP32_BULK)):
+        m = geomhd.Mesh(n, nr, 1.0, 2.0, order, prec=prec, stream=stream.cuda_stream)
+        if U0 is None:
+            U0, phi0 = m.initial_state(make_problem("smooth"))
+        m.upload(U0, phi0)
+        if dt is None:
+            dt = m.cfl_dt(a.cfl)
+        with torch.cuda.stream(stream):
+            for _ in range(a.warmup):
+                m.step(dt)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.steps)]
+        with torch.cuda.stream(stream):
+            for i in range(a.steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                m.step(dt)
+                ev[i][1].record(stream)
+        barrier()
+        t_ms = max_over_ranks(sum(s_.elapsed_time(e) for s_, e in ev), ws, "cuda")
+        out[key] = {"value": replica_throughput(m.Z, a.steps, t_ms, ws), "unit": "zone-updates/s",
+                    "ms_per_step": t_ms / a.steps}
+        m.close()
+    return out
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -450,6 +492,7 @@ def gpu_arm(a):
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
     fp32 = None if (a.no_fp32 or a.fp32_only) else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
+    extra = None if a.no_extra else extra_workload(a, stream, flush, barrier, ws)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
@@ -475,6 +518,8 @@ def gpu_arm(a):
         }
         if fp32 is not None:
             line["fp32_bulk"] = fp32
+        if extra is not None:
+            line["order3_196608"] = extra
         if not a.no_cpu_baseline:
             try:
                 line["cpu_baseline"] = cpu_baseline(a)

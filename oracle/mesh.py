@@ -221,10 +221,16 @@ class Mesh:
     def scaled_moments(self, geo_of, xc0, l00, exps):
         """<((x - xc0)/l00)^e> over the zones described by geo_of -> (nz, ne)."""
         s = (geo_of["xg"] - xc0[:, None, :]) / l00[:, None, None]
-        vals = np.ones(s.shape[:2] + (len(exps),))
+        # integer powers by repeated products: pw[d][k] = s_d^k
+        pw = []
         for d in range(3):
-            vals *= s[..., d:d + 1] ** exps[None, None, :, d]
-        return np.einsum("zp,zpe->ze", geo_of["dV"], vals) / geo_of["V"][:, None]
+            pw.append([np.ones(s.shape[:2])])
+            for _ in range(int(exps[:, d].max())):
+                pw[d].append(pw[d][-1] * s[..., d])
+        vals = np.empty((s.shape[0], len(exps), s.shape[1]))
+        for j, (a, b, c) in enumerate(exps):
+            vals[:, j] = pw[0][a] * pw[1][b] * pw[2][c]
+        return (vals @ geo_of["dV"][:, :, None])[..., 0] / geo_of["V"][:, None]
 
     # ------------------------------------------------------ faces and edges
     def face_geometry(self, X, lf):

@@ -25,7 +25,10 @@ in-sphere diameter of a tangential polyhedron), c_f,max^2 = gamma p/rho + B^2/rh
 Pinned by: tests/test_oracle_step.py -- free-stream preservation of a uniform state
 on the curved mesh, discrete div B at rounding every step, conservation of mass
 and energy up to the boundary-flux ledger, and the design order of accuracy on
-the exact advected entropy wave.
+the exact advected entropy wave; the CFL step of a uniform state against the
+closed-form in-sphere diameter 6V/S of the exact spherical frustum (gnomonic
+solid angle, great-circle side sectors), which the mapped zones approach at the
+map's order; divB on hand-built fields with known per-zone divergence.
 """
 import numpy as np
 
@@ -199,18 +202,23 @@ class Oracle:
 
     # ------------------------------------------------------------- diagnostics
     def cfl_dt(self, U, cfl):
-        m = self.mesh
-        rho, v, p, B = primitives(U, self.gamma)
-        cf = np.sqrt(self.gamma * p / rho + (B * B).sum(-1) / rho)
-        S = self.dfb.area.sum(1)
-        d = 6.0 * self.V / S
-        return cfl * np.min(d / (np.linalg.norm(v, axis=-1) + cf))
+        return cfl_time_step(U, self.V, self.dfb.area.sum(1), self.gamma, cfl)
 
     def divB(self, phi):
         m = self.mesh
         div = (m.zone_face_sign * phi[m.zone_face]).sum(1)
         scale = np.abs(phi[m.zone_face]).sum(1)
         return np.abs(div).max(), (np.abs(div) / np.maximum(scale, 1e-300)).max()
+
+
+def cfl_time_step(U, V, S, gamma, cfl):
+    """dt = cfl min_z d_z / (|v_z| + c_f,max,z) with d_z = 6 V_z / S_z, the in-sphere
+    diameter of a tangential polyhedron of volume V_z and surface S_z (Sec. VII.b),
+    and c_f,max^2 = gamma p / rho + B^2 / rho."""
+    rho, v, p, B = primitives(U, gamma)
+    cf = np.sqrt(gamma * p / rho + (B * B).sum(-1) / rho)
+    d = 6.0 * V / S
+    return cfl * np.min(d / (np.linalg.norm(v, axis=-1) + cf))
 
 
 from . import refelem  # noqa: E402  (used in table construction above)

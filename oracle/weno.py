@@ -19,13 +19,22 @@ which are not available.  Readings (the GPU path implements the same ones):
   * Smoothness: beta = sum_{1<=|a|<=p-1} <(d^a_s P)^2>_0, each multi-index a once.
   * AO combination (Balsara, Garain & Shu 2016 family):
       P = (w_H/g_H)(P_H - sum_k g_k P_k) + sum_k w_k P_k,
-    g_H = 0.85, g_k = 0.15/8, eps = 1e-12, and WENO-Z type nonlinear weights
+    g_H = 0.85, g_k = 0.15/8, and WENO-Z type nonlinear weights (Borges,
+    Carmona, Costa & Don 2008)
       w_m ~ g_m (1 + (tau / (beta_m + eps))^2),  tau = (1/8) sum_k |beta_H - beta_k|,
-    normalised.  Sec. VII states that the schemes reach their design accuracy from
-    the coarsest mesh on (Tables IIa-c); weights g_m/(beta_m + eps)^2 do not on the
-    configured meshes (their octant indicators differ from the central one by
-    tens of percent there, and the weights stay far from the linear ones), while
-    with tau the deviation from the linear weights is of third order in that spread.
+    normalised, with a mesh-dependent eps (Arandiga, Baeza, Belda & Mulet 2011:
+    eps = K h^2 keeps the weights at their linear values to O(h^2) in smooth
+    regions, critical points included, while a jump, whose indicators stay O(1),
+    still selects the smooth stencils):
+      eps = eps_0 + K (l_0 / r_0)^2 u_0^2,   eps_0 = 1e-12, K = 1,
+    h = l_0 / r_0 the zone size relative to the radius of its centroid (so eps is
+    the same along a self-similar radial column) and u_0 the zone average of the
+    variable (so the weights do not change when the data are scaled).  Sec. VII
+    states that the schemes reach their design accuracy from the coarsest mesh on
+    (Tables IIa-c).  With eps = 1e-12 alone they do not on the configured meshes:
+    near critical points and wherever the linear octant fits are far from the
+    central fit, tau / beta stays O(1), and at order 4 the central weight fell to a
+    median 0.1-0.6 of its linear 0.85 on 4-12 columns per cube edge.
   * Variables: all eight conserved components, componentwise (Sec. VI step 2).
   * Boundaries: ghost zones continue the log shells (geometry); their data are
     copies of the boundary shell (continuative outflow, Sec. VII).
@@ -35,8 +44,11 @@ reproduced exactly for every p; the central least-squares fit reproduces every
 polynomial of degree <= p-1 exactly on the curved mapped zones; smoothness of the
 central stencil equals the analytic integral for a known polynomial; the weights
 are exactly linear for equal indicators, deviate from linear at (at least) second
-order in the indicators' relative spread, and favour the smooth octants at a jump.
-parity unpinned (only by invariants): the constants g_H, g_k, eps and the
+order in the indicators' relative spread, and favour the smooth octants at a jump
+(with eps_0 and with the mesh-dependent eps); on smooth data the full nonlinear
+reconstruction converges at the design order p and its error stays within a few
+percent of the linear-weight (central least-squares) error at p = 2, 3, 4.
+parity unpinned (only by invariants): the constants g_H, g_k, eps_0, K and the
 stencil choices are readings, not values the paper fixes.
 """
 import itertools
@@ -47,18 +59,25 @@ from .mesh import taylor_exponents
 
 GAMMA_H = 0.85
 GAMMA_K = 0.15 / 8.0
-EPS = 1e-12
+EPS = 1e-12          # eps_0
+K_EPS = 1.0          # K of eps = eps_0 + K (l_0/r_0)^2 u_0^2
 
 
-def nonlinear_weights(bH, bK):
+def nonlinear_weights(bH, bK, eps=EPS):
     """Normalised WENO-AO weights from the central indicator bH (...) and the eight
     octant indicators bK (..., 8): w_m ~ g_m (1 + (tau/(beta_m + eps))^2) with
-    tau the mean |bH - bK|."""
+    tau the mean |bH - bK|; eps is a scalar or has the shape of bH."""
+    eps = np.asarray(eps, dtype=np.float64)
     tau = np.abs(bH[..., None] - bK).mean(-1)
-    tH = GAMMA_H * (1.0 + (tau / (bH + EPS)) ** 2)
-    tK = GAMMA_K * (1.0 + (tau[..., None] / (bK + EPS)) ** 2)
+    tH = GAMMA_H * (1.0 + (tau / (bH + eps)) ** 2)
+    tK = GAMMA_K * (1.0 + (tau[..., None] / (bK + eps[..., None])) ** 2)
     tot = tH + tK.sum(-1)
     return tH / tot, tK / tot[..., None]
+
+
+def weno_eps(eta, u0):
+    """eps = eps_0 + K eta u0^2 with eta = (l_0 / r_0)^2 of the zone."""
+    return EPS + K_EPS * eta * u0 * u0
 
 # local face -> side index (s, e, n, w) of the column
 LF_SIDE = {0: 3, 1: 1, 2: 0, 3: 2}
@@ -142,7 +161,7 @@ def smoothness_matrix(s, dV, V, exps, p):
                         coef *= (e[ax] - t)
                 r = e - a
                 d[:, :, j] = coef * s[..., 0] ** r[0] * s[..., 1] ** r[1] * s[..., 2] ** r[2]
-            Q += np.einsum("zp,zpi,zpj->zij", dV, d, d) / V[:, None, None]
+            Q += np.swapaxes(d * dV[..., None], 1, 2) @ d / V[:, None, None]
     return Q
 
 
@@ -171,6 +190,8 @@ class WenoAO:
         self.zext = zc * nre + zk + self.g
         g0 = {key: self.geo_ext[key][self.zext] for key in ("V", "xc", "l0", "xg", "dV")}
         self.geo0 = g0
+        # eps scale of the nonlinear weights: (l_0 / |x_0|)^2 per zone
+        self.eta = (g0["l0"] / np.linalg.norm(g0["xc"], axis=-1)) ** 2
         # Taylor-basis means over zone 0 (the constants of Eq. 3.1)
         self.mean0 = m.scaled_moments(g0, g0["xc"], g0["l0"], self.exps)
         nmax = max(len(s) for s in st.central)
@@ -232,7 +253,8 @@ class WenoAO:
             # kink moves the weights by nothing (tau << eps), so it is not recorded
             sb = bH[:, None, :] + bK
             physics.record("weno", np.where(sb > 1e-24, (bH[:, None, :] - bK) / np.maximum(sb, 1e-300), 1.0))
-        wH, wK = nonlinear_weights(bH, np.moveaxis(bK, 1, -1))    # (Z, 8var), (Z, 8var, 8oct)
+        eps = weno_eps(self.eta[:, None], U)                      # (Z, 8var)
+        wH, wK = nonlinear_weights(bH, np.moveaxis(bK, 1, -1), eps)  # (Z, 8var), (Z, 8var, 8oct)
         wK = np.moveaxis(wK, -1, 1)                               # (Z, 8oct, 8var)
         out = (wH / GAMMA_H)[..., None] * uH
         lin = uH[..., :3] - GAMMA_K * uK.sum(1)

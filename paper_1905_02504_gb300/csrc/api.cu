@@ -242,16 +242,23 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.sv_fn = m->upload(T.sv_fn, err);
   D.sv_t = m->upload(T.sv_t, err);
   D.sv_dlw = m->upload(T.sv_dlw, err);
+  // (l_0 / |x_0|)^2 per column: the WENO-AO eps scale
+  std::vector<double> weta(T.ncol);
+  for (int c = 0; c < T.ncol; ++c) {
+    const double* x = &T.xc0[3 * c];
+    weta[c] = T.l0[c] * T.l0[c] / (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  }
   // bulk-arithmetic views of the per-column matrices
   D.b64 = geo::BulkTables<double>{D.pinvH, D.oct_inv, D.Q,        D.TF,       D.nF,       D.wF,
                                   D.GB,    D.TN,      D.J0,       D.iJ0,      D.Sm,       D.gcl,
                                   D.JF,    D.JE,      D.se_t,     D.se_nang,  D.se_nradL, D.se_nradR,
-                                  D.sv_fn, D.sv_t};
+                                  D.sv_fn, D.sv_t,    m->upload(weta, err)};
   const bool f32 = prec == GEO_FP32_BULK;
   if (f32) {
     geo::BulkTables<float>& b = D.b32;
     b.pinvH = m->upload_f32(T.pinvH, err);
     b.oct_inv = m->upload_f32(T.oct_inv, err);
+    b.weta = m->upload_f32(weta, err);
     b.Q = m->upload_f32(T.Q, err);
     b.TF = m->upload_f32(T.TF, err);
     b.nF = m->upload_f32(T.nF, err);

@@ -44,6 +44,9 @@ template <typename R> struct BulkTables {
   const R *pinvH, *oct_inv, *Q, *TF, *nF, *wF, *GB, *TN, *J0, *iJ0, *Sm, *gcl, *JF, *JE;
   // edge geometry: unit tangents and face normals at the edge points
   const R *se_t, *se_nang, *se_nradL, *se_nradR, *sv_fn, *sv_t;
+  // [ncol] (l_0 / |x_0|)^2 of the column's zones (the same along a self-similar
+  // column): the mesh scale of the WENO-AO eps, eps = 1e-12 + weta u_0^2
+  const R* weta;
 };
 
 // Read-only tables in device memory (see host_tables.h for the layouts).

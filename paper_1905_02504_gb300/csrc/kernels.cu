@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
                                               const float* __restrict__ Uhl, R* __restrict__ Wc) {
   using Dm = Dim<P>;
   constexpr int NC1 = Dm::NC1, SMAX = Dm::SMAX;
-  const R GH = R(0.85), GK = R(0.15 / 8.0), EPS = R(1e-12);
+  const R GH = R(0.85), GK = R(0.15 / 8.0), EPS0 = R(1e-12);
   long long z = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (z >= T.Z) return;
   const BulkTables<R>& B = bulk<R>(T);
@@ -88,6 +88,9 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
     const float* Lv = Uhl ? Uhl + static_cast<size_t>(8 + v) * Z : nullptr;
     const double u0d = (sizeof(R) == 8) ? Uv[z] : 0.0;
     const float h0 = (sizeof(R) == 4) ? Hv[z] : 0.f, l0 = (sizeof(R) == 4) ? Lv[z] : 0.f;
+    // eps = eps_0 + K (l_0/r_0)^2 u_0^2 with K = 1 (Arandiga et al. 2011: eps ~ h^2)
+    const R u0 = (sizeof(R) == 8) ? static_cast<R>(u0d) : static_cast<R>(h0);
+    const R EPS = EPS0 + B.weta[c] * u0 * u0;
     auto diff = [&](long long zz) -> R {
       if constexpr (sizeof(R) == 4) return (Hv[zz] - h0) + (Lv[zz] - l0);
       else return static_cast<R>(Uv[zz] - u0d);
@@ -120,6 +123,7 @@ __global__ void __launch_bounds__(TPB) k_weno(const DevTables T, const double* _
       tau += fabs(bH - wK[o]);
     }
     // WENO-Z type weights g (1 + (tau / (beta + eps))^2), tau = mean |beta_H - beta_k|
+    // (Borges, Carmona, Costa & Don 2008), with the mesh-dependent eps above
     tau *= R(0.125);
     const R rH = tau / (bH + EPS);
     R wH = GH * (R(1) + rH * rH);

@@ -257,3 +257,33 @@ def test_fp32_bulk_window_gradient_matches_fp64():
     assert worst < 1e-4 and differs, worst
     m32.close()
     m64.close()
+
+
+def test_window_on_a_side_stream_matches_default_stream():
+    """A mesh created on a torch side stream gives the same window output and
+    gradient as one on the default stream: the binding orders the mesh stream
+    after torch's current stream (inputs written by torch) and torch's current
+    stream after the mesh stream (outputs written by the library)."""
+    import torch
+    from paper_1905_02504_gb300 import autodiff, geomhd
+    K = 2
+    o, m0, U, phi = setup_case(3, 3, 3)
+    dt = o.cfl_dt(U, 0.4)
+    side = torch.cuda.Stream()
+    m1 = geomhd.Mesh(3, 3, 1.0, 2.0, 3, stream=side.cuda_stream)
+    outs = []
+    for mesh in (m0, m1):
+        # torch writes the inputs on its current stream right before the call
+        Ut = torch.from_numpy(np.ascontiguousarray(U.T)).cuda()
+        pt = torch.from_numpy(phi.copy()).cuda()
+        Ut = (Ut * 1.0).requires_grad_(True)
+        pt = (pt * 1.0).requires_grad_(True)
+        UK, pK = autodiff.step_window(mesh, Ut, pt, dt, K)
+        J = autodiff.outer_br2(mesh, pK)
+        J.backward()
+        outs.append((UK.detach().cpu().numpy(), pK.detach().cpu().numpy(),
+                     Ut.grad.cpu().numpy(), pt.grad.cpu().numpy()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    m1.close()
+    m0.close()

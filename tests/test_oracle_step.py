@@ -1,10 +1,13 @@
 """Pins of the oracle's full step (Sec. VI): free-stream preservation, discrete div B,
-conservation with the boundary-flux ledger, and (opt-in, slow) the design order."""
+conservation with the boundary-flux ledger, the design order (one-step error on a
+thin shell by default; the global error on full spheres opt-in, slow), the CFL
+step against closed-form frustums, and divB on hand-built fields."""
 import os
 
 import numpy as np
 import pytest
 
+from oracle import mesh as M
 from oracle.step import Oracle
 from paper_1905_02504_gb300.inputs import make_problem
 
@@ -71,3 +74,111 @@ def test_design_order_entropy_wave():
         mask = (r > 1.3) & (r < 1.7)
         errs.append(np.sum(np.abs(U[:, 0] - ex)[mask] * g["V"][mask]) / np.sum(g["V"][mask]))
     assert np.log2(errs[0] / errs[1]) > 1.8
+
+
+def test_one_step_error_design_order_thin_shell():
+    """Design order of the full step (Sec. VII, Tables IIa-c), p = 2, run by default:
+    one step of dt = 0.2 h on the exact advected entropy wave (v = (0.5,0.5,0.5),
+    uniform p and B) from exact zone averages.  The one-step error of rho is the
+    local truncation error, O(dt h^p) = O(h^(p+1)).  Thin shells of five zones
+    (size h ~ pi r / (2 n) in every direction, middle shell at r = 1.5) keep it
+    cheap; only the middle shell is scored, which no ghost-shell copy reaches in
+    one step (ghost data enter the boundary shells' reconstructions, and through
+    their face fluxes the next shell)."""
+    p, nr, g = 2, 5, 2
+    errs, hs = [], []
+    for n in (6, 12):
+        q = np.exp(np.pi / (2 * n))
+        o = Oracle(n, nr, 1.5 / q ** (g + 0.5), 1.5 * q ** (nr - g - 0.5), p)
+        pr = make_problem("entropy", v0=(0.5, 0.5, 0.5), B0=(0.2, 0.1, -0.1))
+        U, phi = o.initial_state(pr)
+        mid = (np.arange(o.mesh.Z) % nr) == g
+        geo = o.weno.geo0
+        h = geo["l0"][mid].mean()
+        dt = 0.2 * h
+        U1, _ = o.step(U, phi, dt)
+        ex = np.einsum("zg,zg->z", geo["dV"], pr.primitive(geo["xg"] - dt * 0.5)[0]) / geo["V"]
+        errs.append(np.abs(U1[:, 0] - ex)[mid].mean())
+        hs.append(h)
+    assert np.log(errs[0] / errs[1]) / np.log(hs[0] / hs[1]) >= p + 1 - 0.3, errs
+
+
+def _frustum_d(m):
+    """6V/S of the exact spherical frustum of every zone: V = (r1^3 - r0^3) Omega / 3
+    with Omega the solid angle of the gnomonic rectangle [x0,x1] x [y0,y1] on the
+    cube face (x = tan alpha), sum of +-atan(x y / sqrt(1 + x^2 + y^2)); S = the two
+    spherical caps (r0^2 + r1^2) Omega plus four planar side sectors
+    (r1^2 - r0^2) theta / 2, theta the great-circle arc of the side."""
+    d = 0.5 * np.pi / m.n
+    a0 = -0.25 * np.pi + m.col_i * d
+    b0 = -0.25 * np.pi + m.col_j * d
+    x0, x1, y0, y1 = np.tan(a0), np.tan(a0 + d), np.tan(b0), np.tan(b0 + d)
+    F = lambda x, y: np.arctan(x * y / np.sqrt(1.0 + x * x + y * y))
+    omega = F(x1, y1) - F(x0, y1) - F(x1, y0) + F(x0, y0)
+
+    def P(x, y):
+        v = np.stack([x, y, np.ones_like(x)], -1)
+        return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+    arc = lambda a, b: np.arccos(np.clip((a * b).sum(-1), -1.0, 1.0))
+    p00, p10, p01, p11 = P(x0, y0), P(x1, y0), P(x0, y1), P(x1, y1)
+    theta = arc(p00, p10) + arc(p01, p11) + arc(p00, p01) + arc(p10, p11)
+    k = np.arange(m.nr)
+    r0, r1 = m.radius(k)[None, :], m.radius(k + 1)[None, :]
+    V = (r1 ** 3 - r0 ** 3) / 3.0 * omega[:, None]
+    S = (r0 ** 2 + r1 ** 2) * omega[:, None] + 0.5 * (r1 ** 2 - r0 ** 2) * theta[:, None]
+    return (6.0 * V / S).ravel()          # zone order z = c nr + k
+
+
+def _mapped_d(m):
+    from oracle import weno
+    from oracle.divfree import DivFreeB
+    w = weno.WenoAO(m)
+    area = DivFreeB(m, w).area
+    return w.geo0["V"], area.sum(1)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_cfl_step_of_uniform_state_against_exact_frustum(p):
+    """Sec. VII.b: dt = cfl min d_z / (|v| + c_f) with the in-sphere diameter d_z.
+    For a uniform state the oracle's dt must equal cfl min_z 6V/S / (|v| + c_f)
+    of the exact spherical frustums, up to the isoparametric map's geometric error,
+    which shrinks as the mesh is refined (c_f from the closed form
+    sqrt(gamma p / rho + |B|^2 / rho) of the uniform state)."""
+    from oracle.physics import conserved
+    from oracle.step import cfl_time_step
+    g = 5.0 / 3.0
+    rho, v, pr, B = 1.3, np.array([0.4, -0.3, 0.2]), 0.8, np.array([0.3, -0.2, 0.5])
+    cf = np.sqrt(g * pr / rho + (B * B).sum() / rho)
+    errs = []
+    for n in (4, 8):
+        m = M.Mesh(n, 3, 1.0, 1.6, p)
+        U = np.tile(conserved(np.array(rho), v, np.array(pr), B, g), (m.Z, 1))
+        V, S = _mapped_d(m)
+        dt = cfl_time_step(U, V, S, g, 0.4)
+        exact = 0.4 * _frustum_d(m).min() / (np.linalg.norm(v) + cf)
+        errs.append(abs(dt / exact - 1.0))
+        # every zone, not only the smallest
+        errs[-1] = max(errs[-1], np.abs(6.0 * V / S / _frustum_d(m) - 1.0).max())
+    assert errs[1] < {2: 2e-2, 3: 2e-3, 4: 2e-4}[p], errs
+    assert errs[1] < errs[0] / 3.0, errs
+
+
+def test_divb_of_hand_built_fields():
+    """divB = max_z |sum_f s_zf Phi_f| and max_z of that over sum_f |Phi_f|:
+    Phi = s_zf on the six faces of one zone (0 elsewhere) gives divergence 6 in
+    that zone and -1 in each face neighbour (relative value 1 in both); the curl
+    of integer edge values is divergence-free exactly."""
+    from oracle.step import Oracle
+    o = Oracle(3, 3, 1.0, 2.0, 2)
+    m = o.mesh
+    z = m.Z // 2 + 1
+    phi = np.zeros(m.F)
+    phi[m.zone_face[z]] = m.zone_face_sign[z]
+    a, r = o.divB(phi)
+    assert a == 6.0 and r == 1.0
+    div = (m.zone_face_sign * phi[m.zone_face]).sum(1)
+    assert div[z] == 6.0 and np.sort(div)[:6].tolist() == [-1.0] * 6 and (div != 0).sum() == 7
+    e = np.random.default_rng(3).integers(-5, 6, m.E).astype(np.float64)
+    a, r = o.divB((m.face_edge_sign * e[m.face_edges]).sum(1))
+    assert a == 0.0 and r == 0.0
