@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurement")
     ap.add_argument("--compare-steps", type=int, default=10)
-    ap.add_argument("--problem", default="smooth", choices=["smooth", "blast", "lowbeta"])
+    ap.add_argument("--problem", default="smooth",
+                    choices=["smooth", "blast", "lowbeta", "sod", "briowu", "ryujones"],
+                    help="workload; the spherical shock tubes use their own shells (inputs.DOMAINS)")
     ap.add_argument("--noise", type=float, default=0.0, help="seeded relative density noise")
     ap.add_argument("--positivity", action="store_true")
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-bulk form")
@@ -66,8 +68,9 @@ def parse():
     ap.add_argument("--orders", default="2,3,4")
     ap.add_argument("--t-end", type=float, default=0.1)
     ap.add_argument("--shell", default="1.3,1.7", help="radius band of the error norm")
-    ap.add_argument("--predictor", type=int, default=None, choices=[0, 1],
-                    help="predictor schedule: 0 one thread per zone, 1 one thread per node (default: per form)")
+    ap.add_argument("--predictor", type=int, default=None, choices=[0, 1, 2],
+                    help="predictor schedule: 0 one thread per zone, 1 one thread per node, 2 the node team "
+                         "with the contraction in the variable layout (default: the library's)")
     ap.add_argument("--sample-n", type=int, default=4)
     ap.add_argument("--sample-nr", type=int, default=4)
     return ap.parse_args()
@@ -86,11 +89,17 @@ def workload_name(a):
         6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order, form, getattr(a, "problem", "smooth"), extra)
 
 
-def kernel_name(stage, pred):
-    """Name of the kernel that runs a stage (the predictor stage has two schedules)."""
+def kernel_name(stage, pred, positivity=False):
+    """Name of the kernel that runs a stage (the predictor stage has three
+    schedules; the variable-layout one runs the node team when positivity is on)."""
     name = "k_" + stage
-    if stage == "ader" and (pred is None or pred == 1):
-        name += "_team"
+    if stage == "ader":
+        if pred is None:
+            pred = 1
+        if pred == 2 and not positivity:
+            name += "_vt"
+        elif pred != 0:
+            name += "_team"
     return name
 
 
@@ -98,7 +107,7 @@ def sched_name(pred, fp32):
     """Predictor schedule in use (the library default is the node team)."""
     if pred is None:
         pred = 1
-    return "node-team" if pred == 1 else "zone-thread"
+    return {0: "zone-thread", 1: "node-team", 2: "variable-team"}[pred]
 
 
 def max_over_ranks(x, ws, device):
@@ -187,9 +196,10 @@ ORACLE_SNIPPET = r"""
 import json, os, sys, time
 sys.path.insert(0, %(root)r)
 from oracle.step import Oracle
-from paper_1905_02504_gb300.inputs import make_problem
-o = Oracle(%(n)d, %(nr)d, 1.0, 2.0, %(p)d, positivity=%(pos)r)
-U, phi = o.initial_state(make_problem(%(problem)r, noise=%(noise)r))
+from paper_1905_02504_gb300.inputs import domain, make_problem
+pr = make_problem(%(problem)r, noise=%(noise)r)
+o = Oracle(%(n)d, %(nr)d, *domain(%(problem)r), %(p)d, gamma=pr.gamma, positivity=%(pos)r)
+U, phi = o.initial_state(pr)
 dt = o.cfl_dt(U, %(cfl)r)
 times = []
 for s in range(%(steps)d):
@@ -295,7 +305,9 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
     import torch
     from paper_1905_02504_gb300 import geomhd
     sid = stream.cuda_stream
-    m32 = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, prec=geomhd.GEO_FP32_BULK, stream=sid)
+    from paper_1905_02504_gb300.inputs import domain, make_problem
+    m32 = geomhd.Mesh(a.n, a.nr, *domain(a.problem), a.order, prec=geomhd.GEO_FP32_BULK, stream=sid,
+                      gamma=make_problem(a.problem).gamma)
     if a.predictor is not None:
         geomhd.geo_set_predictor(m32.h, a.predictor)
     if a.positivity:
@@ -341,7 +353,7 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": achieved / nominal_fp32,
                      "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], m32.Z, "fp32"),
-                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor),
+                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity),
                      "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
                                   "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
                      "measured_fp32_fma_tflops": fp32_probe},
@@ -409,7 +421,9 @@ def gpu_arm(a):
     stream = torch.cuda.Stream()
     sid = stream.cuda_stream
     prec = geomhd.GEO_FP32_BULK if a.fp32_only else geomhd.GEO_FP64
-    mesh = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, prec=prec, stream=sid)
+    from paper_1905_02504_gb300.inputs import domain
+    mesh = geomhd.Mesh(a.n, a.nr, *domain(a.problem), a.order, prec=prec, stream=sid,
+                       gamma=make_problem(a.problem).gamma)
     if a.predictor is not None:
         geomhd.geo_set_predictor(mesh.h, a.predictor)
     if a.positivity:
@@ -488,7 +502,7 @@ def gpu_arm(a):
     roofline = {"bound": "alu", "achieved": achieved, "peak": nominal, "unit": "TFLOP/s",
                 "frac": achieved / nominal,
                 "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], Z, "fp32" if a.fp32_only else "fp64"),
-                "kernel": kernel_name(geomhd.STAGES[top], a.predictor), "peak_kind": kind, "measured_fma_tflops": fma_peak}
+                "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), "peak_kind": kind, "measured_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
     fp32 = None if (a.no_fp32 or a.fp32_only) else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)

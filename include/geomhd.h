@@ -98,14 +98,18 @@ int geo_set_gamma(geo_mesh_t mesh, double gamma);
 int geo_set_positivity(geo_mesh_t mesh, int enable);
 
 /* Execution schedule of the predictor stage (a2 zone part + a3, Sec. IV.b steps
- * 8-10 and Eqs. C.34-C.36); both compute the same arithmetic:
+ * 8-10 and Eqs. C.34-C.36); all compute the same arithmetic:
  *   GEO_PRED_ZONE_THREAD (0): one thread per zone, its nodal states in
  *     thread-local memory;
  *   GEO_PRED_NODE_TEAM (1, default): one thread per serendipity node, a team of
- *     N threads per zone exchanging nodal fluxes through shared memory.
- * The two differ only in the summation order of the flux-difference rows.
+ *     N threads per zone exchanging nodal fluxes through shared memory;
+ *   GEO_PRED_VAR_TEAM (2): the node team, with the derivative contraction and
+ *     the face / edge point evaluations done by one thread per (zone, variable,
+ *     row group) on the compiled nonzero pattern of D^alpha; with positivity on
+ *     the node-team kernel runs instead.
+ * They differ only in the summation order of the flux-difference rows.
  * Returns GEO_ERR_ARG for any other value. */
-enum { GEO_PRED_ZONE_THREAD = 0, GEO_PRED_NODE_TEAM = 1 };
+enum { GEO_PRED_ZONE_THREAD = 0, GEO_PRED_NODE_TEAM = 1, GEO_PRED_VAR_TEAM = 2 };
 int geo_set_predictor(geo_mesh_t mesh, int schedule);
 
 /* Zone cubature for initial data (host buffers, caller-owned):
@@ -119,6 +123,18 @@ int geo_zone_cubature(geo_mesh_t mesh, int nq, double* pts, double* w);
  * the edge's canonical direction; nq in 1..12 (Gauss-Legendre).  Used to set
  * divergence-free face fluxes from an edge circulation (paper Sec. VIII). */
 int geo_edge_quadrature(geo_mesh_t mesh, int nq, double* pts, double* tw);
+
+/* Face quadrature of the radial faces f = c (nr + 1) + k (host buffers):
+ * pts double[ncol (nr + 1)][nq^2][3] physical points, wn double[...][nq^2][3] =
+ * weight * (h_xi x h_eta), the area element along the face's canonical +r
+ * normal; nq in 1..12 (tensor Gauss-Legendre on the mapped face).  For fields
+ * given by their flux rather than by a vector potential, such as the radial
+ * field B_r ~ sin(theta) / r^2 of the spherical shock tubes (paper Sec.
+ * VIII.c), which has net flux through every sphere: the radial faces of a
+ * column are exact scalings of one another, so the flux of an r^-2 radial field
+ * is the same through all of them and each zone stays divergence-free, while
+ * the angular faces (planes through the origin) carry none of it. */
+int geo_radial_face_quadrature(geo_mesh_t mesh, int nq, double* pts, double* wn);
 
 /* phi[f] = sum over the face's edges of sign * circ[e] (discrete Stokes;
  * host buffers circ double[E], phi double[F]).  The result is exactly

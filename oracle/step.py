@@ -123,6 +123,19 @@ class Oracle:
                 tw = (-1.0 if zrev else 1.0) * h * wq[:, None]
                 circ[e] = problem.edge_circulation(x[None], tw[None])[0]
         phi = (m.face_edge_sign * circ[m.face_edges]).sum(1)
+        if getattr(problem, "has_radial_flux", lambda: False)():
+            # fields given by their flux (the r^-2 radial field of the shock tubes,
+            # Sec. VIII.c): the face rule over each radial face, normal along +r;
+            # face (c, k) is the inner face of zone (c, k), the last the outer face
+            # of the last shell
+            fin, fout = self.dfb.fgeo[4], self.dfb.fgeo[5]
+            z = np.arange(m.Z)
+            c, k = z // m.nr, z % m.nr
+            wn = -fin["n"] * (fin["w"][None, :] * fin["dA"])[..., None]
+            phi[c * (m.nr + 1) + k] += problem.radial_face_flux(fin["x"], wn)
+            last = z[k == m.nr - 1]
+            wn = fout["n"][last] * (fout["w"][None, :] * fout["dA"][last])[..., None]
+            phi[c[last] * (m.nr + 1) + m.nr] += problem.radial_face_flux(fout["x"][last], wn)
         return U, phi
 
     # ------------------------------------------------------------------ step

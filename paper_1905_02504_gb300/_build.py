@@ -19,6 +19,15 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["host_tables.cpp", "kernels.cu", "api.cu", "noalloc.cu"]
 
 
+def _refpattern():
+    """The generator of refpattern.h (loaded by path: this file also runs as a script)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_geomhd_refpattern", os.path.join(HERE, "refpattern.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def _nvcc():
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     path = os.path.join(cuda, "bin", "nvcc")
@@ -27,11 +36,11 @@ def _nvcc():
 
 def _flags(extra=()):
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3",
-                   "-I" + INC, "-I" + SRC] + list(extra)
+                   "-I" + INC, "-I" + SRC, "-I" + BUILD] + list(extra)
 
 
 def _deps():
-    files = [os.path.join(SRC, f) for f in os.listdir(SRC)]
+    files = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(HERE, "refpattern.py")]
     files += [os.path.join(INC, f) for f in os.listdir(INC)]
     return files
 
@@ -48,6 +57,7 @@ def build(verbose=False, ptxas_info=False, force=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
+    _refpattern().write(os.path.join(BUILD, "refpattern.h"))
     nvcc = _nvcc()
 
     def compile_one(src):

@@ -249,16 +249,22 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
     weta[c] = T.l0[c] * T.l0[c] / (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   }
   // bulk-arithmetic views of the per-column matrices
+  std::vector<double> iJF(T.JF.size()), iJE(T.JE.size());
+  for (size_t t = 0; t < iJF.size(); ++t) iJF[t] = 1.0 / T.JF[t];
+  for (size_t t = 0; t < iJE.size(); ++t) iJE[t] = 1.0 / T.JE[t];
   D.b64 = geo::BulkTables<double>{D.pinvH, D.oct_inv, D.Q,        D.TF,       D.nF,       D.wF,
                                   D.GB,    D.TN,      D.J0,       D.iJ0,      D.Sm,       D.gcl,
                                   D.JF,    D.JE,      D.se_t,     D.se_nang,  D.se_nradL, D.se_nradR,
-                                  D.sv_fn, D.sv_t,    m->upload(weta, err)};
+                                  D.sv_fn, D.sv_t,    m->upload(weta, err), m->upload(iJF, err),
+                                  m->upload(iJE, err)};
   const bool f32 = prec == GEO_FP32_BULK;
   if (f32) {
     geo::BulkTables<float>& b = D.b32;
     b.pinvH = m->upload_f32(T.pinvH, err);
     b.oct_inv = m->upload_f32(T.oct_inv, err);
     b.weta = m->upload_f32(weta, err);
+    b.iJF = m->upload_f32(iJF, err);
+    b.iJE = m->upload_f32(iJE, err);
     b.Q = m->upload_f32(T.Q, err);
     b.TF = m->upload_f32(T.TF, err);
     b.nF = m->upload_f32(T.nF, err);
@@ -346,7 +352,7 @@ int geo_set_positivity(geo_mesh_t m, int enable) {
 
 int geo_set_predictor(geo_mesh_t m, int schedule) {
   if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
-  if (schedule != GEO_PRED_ZONE_THREAD && schedule != GEO_PRED_NODE_TEAM)
+  if (schedule != GEO_PRED_ZONE_THREAD && schedule != GEO_PRED_NODE_TEAM && schedule != GEO_PRED_VAR_TEAM)
     return fail(GEO_ERR_ARG, "unknown predictor schedule");
   m->dt.predictor = schedule;
   return GEO_OK;
@@ -361,6 +367,12 @@ int geo_zone_cubature(geo_mesh_t m, int nq, double* pts, double* w) {
 int geo_edge_quadrature(geo_mesh_t m, int nq, double* pts, double* tw) {
   if (!m || !pts || !tw || nq < 1 || nq > 12) return fail(GEO_ERR_ARG, "bad quadrature arguments");
   geo::edge_quadrature(m->T, nq, pts, tw);
+  return GEO_OK;
+}
+
+int geo_radial_face_quadrature(geo_mesh_t m, int nq, double* pts, double* wn) {
+  if (!m || !pts || !wn || nq < 1 || nq > 12) return fail(GEO_ERR_ARG, "bad quadrature arguments");
+  geo::radial_face_quadrature(m->T, nq, pts, wn);
   return GEO_OK;
 }
 

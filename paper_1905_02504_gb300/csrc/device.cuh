@@ -33,6 +33,7 @@ template <int P, typename R> struct RefConst {
   R psiEc[12 * Dim<P>::NS * Dim<P>::NEN];       // edge-node basis at the edge points
   unsigned char enode[12 * Dim<P>::NEN];
   R R_[Dim<P>::M * Dim<P>::M];
+  R Dpat[3 * Dim<P>::NNZ];                      // D^alpha at the compiled pattern (refpattern.h)
 };
 
 // Per-column matrices used by the bulk arithmetic, in its type R.  The FP64
@@ -47,6 +48,8 @@ template <typename R> struct BulkTables {
   // [ncol] (l_0 / |x_0|)^2 of the column's zones (the same along a self-similar
   // column): the mesh scale of the WENO-AO eps, eps = 1e-12 + weta u_0^2
   const R* weta;
+  // [ncol][NQT], [ncol][12 NS]: 1 / (interpolated J) at the face and edge points
+  const R *iJF, *iJE;
 };
 
 // Read-only tables in device memory (see host_tables.h for the layouts).

@@ -1282,6 +1282,35 @@ void zone_centroids(const Tables& T, double* xc, double* vol) {
     }
 }
 
+void radial_face_quadrature(const Tables& T, int nq, double* pts, double* wn) {
+  Tables tmp;
+  Builder b(T.n, T.nr, T.r_in, T.r_out, T.d.P, tmp);
+  vector<double> x, wx;
+  gauss_legendre(nq, x, wx);
+  const int G = nq * nq;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int c = 0; c < T.ncol; ++c)
+    for (int k = 0; k <= T.nr; ++k) {
+      // the inner face (zeta = -1/2) of shell k; the outer face of the last shell
+      const int kz = k < T.nr ? k : T.nr - 1;
+      const double zeta = k < T.nr ? -0.5 : 0.5;
+      vector<V3> X = b.zone_nodes(c, kz);
+      const int64_t f = static_cast<int64_t>(c) * (T.nr + 1) + k;
+      for (int a = 0; a < nq; ++a)
+        for (int bb = 0; bb < nq; ++bb) {
+          const V3 xi{x[a], x[bb], zeta};
+          const V3 xx = b.map_point(X, xi);
+          const auto h = b.map_jac(X, xi);
+          const V3 n = cross(h[0], h[1]);  // (h_xi x h_eta): along +r on these faces
+          const int64_t g = f * G + a * nq + bb;
+          for (int d = 0; d < 3; ++d) {
+            pts[g * 3 + d] = xx[d];
+            wn[g * 3 + d] = n[d] * wx[a] * wx[bb];
+          }
+        }
+    }
+}
+
 void face_geometry(const Tables& T, double* area, double* nrm) {
   const int NQT = T.d.NQT;
   auto fill = [&](int64_t f, int c, int lf, int k, double sign) {

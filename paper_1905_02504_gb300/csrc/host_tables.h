@@ -113,5 +113,6 @@ void edge_quadrature(const Tables& T, int nq, double* pts, double* tw);
 void phi_from_circulation(const Tables& T, const double* circ, double* phi);
 void zone_centroids(const Tables& T, double* xc, double* vol);
 void face_geometry(const Tables& T, double* area, double* nrm);
+void radial_face_quadrature(const Tables& T, int nq, double* pts, double* wn);
 
 }  // namespace geo

@@ -11,10 +11,13 @@
 // the time-integrated face fluxes and edge EMFs are accumulated in FP64 and the
 // updates of U and Phi are FP64 in both forms, so div B stays at FP64 rounding.
 #include "device.cuh"
+#include "geomhd.h"
 #include "host_tables.h"
 #include "mhd_device.cuh"
+#include "refpattern.h"  // generated at build time (refpattern.py)
 
 #include <cfloat>
+#include <utility>
 
 namespace geo {
 
@@ -626,40 +629,21 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
   __syncthreads();
 }
 
-// resident blocks per SM the register budget is sized for
-template <int P, typename R> struct TeamOcc;
-template <> struct TeamOcc<2, float> { static constexpr int MINB = 8; };   // 128 threads
-template <> struct TeamOcc<3, float> { static constexpr int MINB = 5; };   // 160 threads (72 registers, a few spilled)
-template <> struct TeamOcc<4, float> { static constexpr int MINB = 4; };   // 128 threads (128 registers, a few spilled)
-template <> struct TeamOcc<2, double> { static constexpr int MINB = 4; };
-template <> struct TeamOcc<3, double> { static constexpr int MINB = 2; };
-template <> struct TeamOcc<4, double> { static constexpr int MINB = 2; };
-
-template <int P, typename R, bool POS>
-__global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
-    k_ader_team(const DevTables T, double* __restrict__ U, const double* __restrict__ phi,
-                const R* __restrict__ Wc, const R* __restrict__ Bp, R* __restrict__ trF, R* __restrict__ trE,
-                double dt) {
+// Zone inputs of a team block into shared memory: the WENO-AO coefficients,
+// the zone means, the KKT right-hand side of the divergence-free reconstruction
+// (zone B modes, nodal normal fields, face means; Sec. IV.b steps 5-8), then the
+// zone-mean B of step 10 (written back to U) and the time-step factor dt / q^k.
+// SM is any shared-memory struct with members in, W, Uz and fs per zone.
+template <int P, typename R, typename SM>
+__device__ __forceinline__ void team_load_inputs(SM& S, const DevTables& T, double* __restrict__ U,
+                                                 const double* __restrict__ phi, const R* __restrict__ Wc,
+                                                 const R* __restrict__ Bp, double dt, long long zbase, int tid) {
   using Dm = Dim<P>;
-  constexpr int N = Dm::N, M = Dm::M, NC1 = Dm::NC1, NC = Dm::NC, NQT = Dm::NQT, NS = Dm::NS,
-                NBIN = Dm::NBIN, NR = 3 + 3 * Dm::N, ZB = Team<P>::ZB, NT = ZB * N;
-  __shared__ TeamSmem<P, R> S;
-  const RefConst<P, R>& K = RC<P, R>::get();
+  constexpr int NC1 = Dm::NC1, NC = Dm::NC, NQT = Dm::NQT, NBIN = Dm::NBIN, NR = 3 + 3 * Dm::N,
+                ZB = Team<P>::ZB, NT = ZB * Dm::N;
   const BulkTables<R>& BT = bulk<R>(T);
   const long long Z = T.Z, F = T.F;
   const int nr = T.nr;
-  const int tid = threadIdx.x;
-  const long long zbase = static_cast<long long>(blockIdx.x) * ZB;
-  // ---- reference tables and zone inputs into shared memory
-  for (int t = tid; t < 3 * Dm::RL * N; t += NT) {
-    S.Ev[t] = K.Eval[t];
-    S.Ec[t] = K.Ecol[t];
-  }
-  for (int t = tid; t < NQT * Dm::NFN; t += NT) S.psiF[t] = K.psiFc[t];
-  for (int t = tid; t < 6 * Dm::NFN; t += NT) S.fnode[t] = K.fnode[t];
-  for (int t = tid; t < 12 * NS * Dm::NEN; t += NT) S.psiE[t] = K.psiEc[t];
-  for (int t = tid; t < 12 * Dm::NEN; t += NT) S.enode[t] = K.enode[t];
-  for (int w = tid; w < ZB * 5; w += NT) S.th[w / 5][w % 5] = R(1);
   for (int w = tid; w < ZB * 3 * NC; w += NT) {
     const int zl = w % ZB, e = w / ZB, d = e / NC, t = e % NC;
     const long long z = zbase + zl;
@@ -716,6 +700,95 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
     }
   }
   __syncthreads();
+}
+
+// Reconstructed conserved values at node i of zone zl (Sec. V.d steps 5-6): the
+// fluid variables from the WENO-AO Taylor coefficients, B from the
+// divergence-free KKT solution; u = 1 for the padding threads of a partial block.
+template <int P, typename R, typename SM>
+__device__ __forceinline__ void team_nodal_values(const SM& S, const BulkTables<R>& BT, int c, int i, int zl,
+                                                  bool valid, R* u) {
+  using Dm = Dim<P>;
+  constexpr int N = Dm::N, NC1 = Dm::NC1, NBIN = Dm::NBIN, NR = 3 + 3 * Dm::N;
+  if (valid) {
+    const R* TN = BT.TN + static_cast<size_t>(c) * N * NC1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R s = S.Uz[zl][v];
+      for (int m = 0; m < NC1; ++m) s += TN[m * N + i] * S.W[zl][v * NC1 + m];
+      u[v] = s;
+    }
+    const R* GB = BT.GB + static_cast<size_t>(c) * NR * NBIN;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R s = R(0);
+      for (int b = 0; b < NBIN; ++b) s += GB[b * NR + 3 + d * N + i] * S.in[zl][b];
+      u[5 + d] = s;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 8; ++v) u[v] = R(1);
+  }
+}
+
+// Metric terms of node i (Eqs. 5.5-5.11): 1/J, the discrete GCL residual g_i and
+// the three contravariant area vectors S^alpha (zeros for padding threads).
+template <int P, typename R>
+__device__ __forceinline__ void team_node_metrics(const BulkTables<R>& BT, int c, int i, bool valid, R& iJ,
+                                                  R* g, R* Sa) {
+  constexpr int N = Dim<P>::N;
+  iJ = R(1);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) g[t] = R(0);
+#pragma unroll
+  for (int t = 0; t < 9; ++t) Sa[t] = R(0);
+  if (valid) {
+    iJ = BT.iJ0[static_cast<size_t>(c) * N + i];
+    const R* gc = BT.gcl + (static_cast<size_t>(c) * N + i) * 3;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) g[t] = gc[t];
+#pragma unroll
+    for (int al = 0; al < 3; ++al)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) Sa[3 * al + t] = BT.Sm[static_cast<size_t>(c) * 9 * N + (al * N + i) * 3 + t];
+  }
+}
+
+// resident blocks per SM the register budget is sized for
+template <int P, typename R> struct TeamOcc;
+template <> struct TeamOcc<2, float> { static constexpr int MINB = 8; };   // 128 threads
+template <> struct TeamOcc<3, float> { static constexpr int MINB = 5; };   // 160 threads (72 registers, a few spilled)
+template <> struct TeamOcc<4, float> { static constexpr int MINB = 4; };   // 128 threads (128 registers, a few spilled)
+template <> struct TeamOcc<2, double> { static constexpr int MINB = 4; };
+template <> struct TeamOcc<3, double> { static constexpr int MINB = 2; };
+template <> struct TeamOcc<4, double> { static constexpr int MINB = 2; };
+
+template <int P, typename R, bool POS>
+__global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
+    k_ader_team(const DevTables T, double* __restrict__ U, const double* __restrict__ phi,
+                const R* __restrict__ Wc, const R* __restrict__ Bp, R* __restrict__ trF, R* __restrict__ trE,
+                double dt) {
+  using Dm = Dim<P>;
+  constexpr int N = Dm::N, M = Dm::M, NC1 = Dm::NC1, NC = Dm::NC, NQT = Dm::NQT, NS = Dm::NS,
+                NBIN = Dm::NBIN, NR = 3 + 3 * Dm::N, ZB = Team<P>::ZB, NT = ZB * N;
+  __shared__ TeamSmem<P, R> S;
+  const RefConst<P, R>& K = RC<P, R>::get();
+  const BulkTables<R>& BT = bulk<R>(T);
+  const long long Z = T.Z, F = T.F;
+  const int nr = T.nr;
+  const int tid = threadIdx.x;
+  const long long zbase = static_cast<long long>(blockIdx.x) * ZB;
+  // ---- reference tables and zone inputs into shared memory
+  for (int t = tid; t < 3 * Dm::RL * N; t += NT) {
+    S.Ev[t] = K.Eval[t];
+    S.Ec[t] = K.Ecol[t];
+  }
+  for (int t = tid; t < NQT * Dm::NFN; t += NT) S.psiF[t] = K.psiFc[t];
+  for (int t = tid; t < 6 * Dm::NFN; t += NT) S.fnode[t] = K.fnode[t];
+  for (int t = tid; t < 12 * NS * Dm::NEN; t += NT) S.psiE[t] = K.psiEc[t];
+  for (int t = tid; t < 12 * Dm::NEN; t += NT) S.enode[t] = K.enode[t];
+  for (int w = tid; w < ZB * 5; w += NT) S.th[w / 5][w % 5] = R(1);
+  team_load_inputs<P, R>(S, T, U, phi, Wc, Bp, dt, zbase, tid);
   // ---- node of this thread (zone-fastest mapping)
   const int zl = tid % ZB, i = tid / ZB;
   const long long z = zbase + zl;
@@ -725,25 +798,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
   R Uh[M][8];
   {
     R u[8];
-    if (valid) {
-      const R* TN = BT.TN + static_cast<size_t>(c) * N * NC1;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        R s = S.Uz[zl][v];
-        for (int m = 0; m < NC1; ++m) s += TN[m * N + i] * S.W[zl][v * NC1 + m];
-        u[v] = s;
-      }
-      const R* GB = BT.GB + static_cast<size_t>(c) * NR * NBIN;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        R s = R(0);
-        for (int b = 0; b < NBIN; ++b) s += GB[b * NR + 3 + d * N + i] * S.in[zl][b];
-        u[5 + d] = s;
-      }
-    } else {
-#pragma unroll
-      for (int v = 0; v < 8; ++v) u[v] = R(1);
-    }
+    team_nodal_values<P, R>(S, BT, c, i, zl, valid, u);
     if constexpr (POS) {
       const R* Uz = S.Uz[zl];
       const R pbar = pressure_of(Uz, gam);
@@ -769,19 +824,8 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
       for (int v = 0; v < 8; ++v) Uh[m][v] = j0 * u[v];
   }
   // ---- metric terms of the node, kept for all flux evaluations
-  R iJ = R(1), g[3] = {R(0), R(0), R(0)}, Sa[9];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) Sa[t] = R(0);
-  if (valid) {
-    iJ = BT.iJ0[static_cast<size_t>(c) * N + i];
-    const R* gc = BT.gcl + (static_cast<size_t>(c) * N + i) * 3;
-#pragma unroll
-    for (int t = 0; t < 3; ++t) g[t] = gc[t];
-#pragma unroll
-    for (int al = 0; al < 3; ++al)
-#pragma unroll
-      for (int t = 0; t < 3; ++t) Sa[3 * al + t] = BT.Sm[static_cast<size_t>(c) * 9 * N + (al * N + i) * 3 + t];
-  }
+  R iJ, g[3], Sa[9];
+  team_node_metrics<P, R>(BT, c, i, valid, iJ, g, Sa);
   // ---- Picard iterations (Eqs. C.34-C.36); in the first iteration every level
   // equals level 1, so its flux difference is reused
   const R fs = S.fs[zl];
@@ -937,6 +981,8 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
     }
   }
 }
+
+#include "ader_vt.cuh"
 
 // ----------------------------------------------------------------------------
 // a4: face fluxes (HLL at face points x Gauss times, FP64 accumulation)
@@ -1396,6 +1442,26 @@ cudaError_t upload_reference_constants(const Tables& T) {
   for (int i = 0; i < 12 * Dm::NS * Dm::NEN; ++i) h.psiEc[i] = static_cast<R>(T.psiEc[i]);
   for (int i = 0; i < 12 * Dm::NEN; ++i) h.enode[i] = static_cast<unsigned char>(T.enode[i]);
   for (int i = 0; i < Dm::M * Dm::M; ++i) h.R_[i] = static_cast<R>(T.R[i]);
+  // values at the compiled pattern of D^alpha; every nonzero of the host's D^alpha
+  // must lie in it, and the face / edge node lists must be the compiled ones
+  {
+    using RP = RefPattern<P>;
+    static_assert(RP::NNZ == Dm::NNZ && RP::NFN == Dm::NFN && RP::NEN == Dm::NEN, "pattern sizes");
+    bool in_pat[3][Dm::N][Dm::N] = {};
+    for (int e = 0; e < 3 * RP::NNZ; ++e) {
+      const int al = e / RP::NNZ, i = RP::I[e], j = RP::J[e];
+      in_pat[al][i][j] = true;
+      h.Dpat[e] = static_cast<R>(T.D[(static_cast<size_t>(al) * Dm::N + i) * Dm::N + j]);
+    }
+    for (int al = 0; al < 3; ++al)
+      for (int j = 0; j < Dm::N; ++j)
+        for (int t = T.Dptr[al * (Dm::N + 1) + j]; t < T.Dptr[al * (Dm::N + 1) + j + 1]; ++t)
+          if (!in_pat[al][T.Drow[al * Dm::NNZ + t]][j]) return cudaErrorInvalidValue;
+    for (int t = 0; t < 6 * Dm::NFN; ++t)
+      if (T.fnode[t] != RP::FN[t]) return cudaErrorInvalidValue;
+    for (int t = 0; t < 12 * Dm::NEN; ++t)
+      if (T.enode[t] != RP::EN[t]) return cudaErrorInvalidValue;
+  }
   // row form of D^alpha, padded to RL entries per row with zeros (column = the row)
   for (int al = 0; al < 3; ++al) {
     int fill[Dm::N] = {};
@@ -1430,7 +1496,11 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
       k_bperp<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp);
       break;
     case ST_ADER:
-      if (T.predictor == 1) {
+      if (T.predictor == GEO_PRED_VAR_TEAM && !T.positivity) {
+        constexpr int ZB = Team<P>::ZB;
+        const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
+        k_ader_vt<P, R><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+      } else if (T.predictor != GEO_PRED_ZONE_THREAD) {
         constexpr int ZB = Team<P>::ZB;
         const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
         if (T.positivity)

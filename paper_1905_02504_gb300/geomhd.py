@@ -46,6 +46,7 @@ _SIGS = {
     "geo_check_state": [_h, ctypes.POINTER(ctypes.c_int)],
     "geo_zone_cubature": [_h, ctypes.c_int, _vp, _vp],
     "geo_edge_quadrature": [_h, ctypes.c_int, _vp, _vp],
+    "geo_radial_face_quadrature": [_h, ctypes.c_int, _vp, _vp],
     "geo_phi_from_edge_circulation": [_h, _vp, _vp],
     "geo_zone_geometry": [_h, _vp, _vp],
     "geo_face_geometry": [_h, _vp, _vp],
@@ -125,6 +126,7 @@ def geo_set_positivity(h, enable):
 
 GEO_PRED_ZONE_THREAD = 0
 GEO_PRED_NODE_TEAM = 1
+GEO_PRED_VAR_TEAM = 2
 
 
 def geo_set_predictor(h, schedule):
@@ -153,6 +155,14 @@ def geo_edge_quadrature(h, nq):
     tw = np.empty((E, nq, 3))
     _check(_lib.geo_edge_quadrature(h, nq, _ptr(pts), _ptr(tw)), "geo_edge_quadrature")
     return pts, tw
+
+
+def geo_radial_face_quadrature(h, nq, nrad):
+    """nrad = ncol (nr + 1), the number of radial faces of the mesh."""
+    pts = np.empty((nrad, nq * nq, 3))
+    wn = np.empty((nrad, nq * nq, 3))
+    _check(_lib.geo_radial_face_quadrature(h, nq, _ptr(pts), _ptr(wn)), "geo_radial_face_quadrature")
+    return pts, wn
 
 
 def geo_phi_from_edge_circulation(h, circ):
@@ -314,6 +324,11 @@ class Mesh:
         epts, tw = geo_edge_quadrature(self.h, nq_edge)
         circ = problem.edge_circulation(epts, tw)
         phi = geo_phi_from_edge_circulation(self.h, circ)
+        if problem.has_radial_flux():
+            n, nr = self.args[0], self.args[1]
+            nrad = 6 * n * n * (nr + 1)
+            fpts, wn = geo_radial_face_quadrature(self.h, nq_edge, nrad)
+            phi[:nrad] += problem.radial_face_flux(fpts, wn)
         return np.ascontiguousarray(U.T), phi
 
     def upload(self, U, phi):

@@ -261,7 +261,7 @@ def test_fp32_bulk_window_gradient_matches_fp64():
 
 def test_window_on_a_side_stream_matches_default_stream():
     """A mesh created on a torch side stream gives the same window output and
-    gradient as one on the default stream: the binding orders the mesh stream
+    gradient (to rounding) as one on the default stream: the binding orders the mesh stream
     after torch's current stream (inputs written by torch) and torch's current
     stream after the mesh stream (outputs written by the library)."""
     import torch
@@ -283,7 +283,11 @@ def test_window_on_a_side_stream_matches_default_stream():
         J.backward()
         outs.append((UK.detach().cpu().numpy(), pK.detach().cpu().numpy(),
                      Ut.grad.cpu().numpy(), pt.grad.cpu().numpy()))
-    for a, b in zip(*outs):
+    # the forward step is deterministic; the reverse sweep scatters into the WENO
+    # stencils with FP64 atomics, so the gradients agree to rounding
+    for a, b in zip(outs[0][:2], outs[1][:2]):
         assert np.array_equal(a, b)
+    for a, b in zip(outs[0][2:], outs[1][2:]):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
     m1.close()
     m0.close()

@@ -32,7 +32,7 @@ def fp32_mesh(n, nr, p, U, phi, schedule=None):
     return m
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2])
 @pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 10), (5, 3, 3, 4), (3, 5, 4, 2)])
 def test_fp32_bulk_error_vs_oracle(n, nr, p, steps, schedule):
     o, m64, U, phi = setup_case(n, nr, p)
@@ -53,7 +53,7 @@ def test_fp32_bulk_error_vs_oracle(n, nr, p, steps, schedule):
     m.close()
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2])
 @pytest.mark.parametrize("p", [2, 3, 4])
 def test_fp32_bulk_free_stream(p, schedule):
     n, nr = (4, 3) if p < 4 else (3, 5)

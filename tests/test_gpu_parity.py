@@ -48,7 +48,9 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-SCHEDULES = [0, 1]   # predictor: one thread per zone; a team of one thread per node
+# predictor: one thread per zone; a team of one thread per node; the team with the
+# contraction and point evaluations in the variable layout
+SCHEDULES = [0, 1, 2]
 _STAGES = {}
 
 

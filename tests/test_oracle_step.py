@@ -182,3 +182,27 @@ def test_divb_of_hand_built_fields():
     e = np.random.default_rng(3).integers(-5, 6, m.E).astype(np.float64)
     a, r = o.divB((m.face_edge_sign * e[m.face_edges]).sum(1))
     assert a == 0.0 and r == 0.0
+
+
+@pytest.mark.parametrize("name", ["briowu", "ryujones"])
+def test_shock_tube_initial_field_divergence_free(name):
+    """Sec. VIII.c: the toroidal field from the edge circulation of A_r and the
+    r^-2 radial field from its flux through the radial faces together give zone
+    divergences at rounding; the radial part alone has the same flux through
+    every radial face of a column (the faces are scalings of one another), and
+    the angular faces carry none of it."""
+    from paper_1905_02504_gb300.inputs import domain
+    r_in, r_out = domain(name)
+    pr = make_problem(name, delta=0.1)
+    o = Oracle(3, 4, r_in, r_out, 3, gamma=pr.gamma)
+    m = o.mesh
+    U, phi = o.initial_state(pr)
+    assert o.divB(phi)[1] < 1e-14
+    # the radial-flux part: initial state minus the circulation part
+    circ_only = make_problem(name, delta=0.1)
+    circ_only.has_radial_flux = lambda: False
+    _, phi_a = o.initial_state(circ_only)
+    rad = (phi - phi_a)[:m.ncol * (m.nr + 1)].reshape(m.ncol, m.nr + 1)
+    assert np.abs(rad - rad[:, :1]).max() < 1e-13 * np.abs(rad).max()
+    assert np.abs(rad).max() > 0.1
+    assert np.array_equal(phi[m.ncol * (m.nr + 1):], phi_a[m.ncol * (m.nr + 1):])
