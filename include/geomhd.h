@@ -209,8 +209,11 @@ int geo_outer_Br2(geo_mesh_t mesh, const double* phi_dev, double* J, double* gph
 int geo_set_stage_timing(geo_mesh_t mesh, int enable);
 int geo_get_stage_timing(geo_mesh_t mesh, double* ms, int64_t* counts);
 
-/* Algorithmic FP64 floating-point operations per zone of one geo_step stage,
- * counted from the loop bounds of the method (order-dependent, host only). */
+/* Algorithmic floating-point operations per unit (zone, face or edge) of one
+ * geo_step stage, counted from the loop bounds of the method (order-dependent,
+ * host only; the same count for the FP64 and the FP32-bulk form; an FMA counts
+ * two).  The predictor's count is cross-checked by an operation-counting pass
+ * of the test oracle's predictor on one zone. */
 int geo_stage_flops(geo_mesh_t mesh, double* flops_per_unit, int64_t* units);
 
 /* Measured FMA throughput of this GPU for the precision: a dependent-chain
@@ -226,6 +229,27 @@ int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s);
  * count = number of doubles the host buffer holds; GEO_ERR_ARG if too small.
  * Synchronises the stream. */
 int geo_debug_buffer(geo_mesh_t mesh, int which, double* host, int64_t count);
+
+/* Test support for stage-by-stage checks (FP64 meshes; host buffers; the calls
+ * synchronise).  geo_debug_set_buffer overwrites work buffer `which` (the
+ * numbering of geo_debug_buffer; count must equal its size);
+ * geo_debug_run_stage launches one forward stage (0 WENO-AO, 1 nodal normal
+ * fields, 2 predictor, 3 face fluxes, 4 edge EMFs, 5 U update, 6 Phi update) on
+ * the mesh's current buffers; geo_debug_stage_vjp applies the transpose of one
+ * stage's Jacobian alone, linearised at the forward intermediates of (U, phi)
+ * (the reverse kernels of geo_step_adjoint, Sec. VI read backwards):
+ *   stage 0 WENO-AO:   g_out = cotangent of the Taylor coefficients [8][NC1][Z]
+ *                      -> g_in = cotangent of U [8][Z]
+ *   stage 2 predictor: g_out = cotangents of the face- then edge-point states
+ *                      -> g_in = cotangent of the Taylor coefficients (with the
+ *                      nodal normal fields and U held fixed)
+ *   stage 3 faces:     g_out = [8][F] -> g_in = cotangent of the face-point states
+ *   stage 4 edges:     g_out = [E]    -> g_in = cotangent of the edge-point states
+ * n_out, n_in must equal those sizes (GEO_ERR_ARG otherwise). */
+int geo_debug_set_buffer(geo_mesh_t mesh, int which, const double* host, int64_t count);
+int geo_debug_run_stage(geo_mesh_t mesh, int stage, double dt);
+int geo_debug_stage_vjp(geo_mesh_t mesh, int stage, double dt, const double* U, const double* phi,
+                        const double* g_out, int64_t n_out, double* g_in, int64_t n_in);
 
 /* CFL time step for callers that cannot allocate device memory at the time of
  * the call (a memory pool owned by another component, a rule against device

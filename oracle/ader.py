@@ -24,7 +24,7 @@ the Gauss times tau_2..tau_M) are U(x, tau_m) = sum_i U_hat_{m,i} psi_i(x) /
 sum_i J_i psi_i(x): the nodal interpolant of J U divided by the interpolant of J
 (so a uniform state stays exactly uniform).
 
-Pinned by: tests/test_oracle_ader.py -- uniform state preserved to rounding on the
+Pinned by: tests/test_oracle_divfree_ader.py -- uniform state preserved to rounding on the
 curved mesh; on an affinely mapped zone, linear advection of a polynomial of
 degree <= p-1 is reproduced exactly in space-time after p iterations; the nodal
 flux-difference row matches Eq. B.16 on the paper's prism.
@@ -54,7 +54,7 @@ class AderPredictor:
         """dF_i of Eq. C.34 (with the geometric-conservation term) for one level."""
         Up = Uh / self.J[..., None]
         g = self.gamma
-        out = np.zeros(Uh.shape)
+        out = np.zeros_like(Uh)
         for a in range(3):
             Fa = dt * flux_dir(Up, self.S[:, a], g)
             out += np.einsum("ij,zjv->ziv", self.el.D[a], Fa)

@@ -24,7 +24,7 @@ Per zone, in the zone's Taylor basis s = (x - x_0)/l_0:
     radial-column amortisation, which only the GPU path uses).
   * Step 10: the zone-centred B becomes the constant terms of the solution.
 
-Pinned by: tests/test_oracle_divfree.py -- for B = curl A with a polynomial A of
+Pinned by: tests/test_oracle_divfree_ader.py -- for B = curl A with a polynomial A of
 degree <= p the reconstruction has div B = 0 identically and reproduces a linear
 field exactly; Eq. 4.13 holds to rounding; the face constraints hold; the mean
 equals the face-consistent value.

@@ -61,7 +61,7 @@ def flux_dir(U, nvec, gamma):
     Bn = (B * nvec).sum(-1)
     pt = p + 0.5 * (B * B).sum(-1)
     vB = (v * B).sum(-1)
-    F = np.empty(U.shape)
+    F = np.empty_like(U)
     F[..., RHO] = rho * vn
     F[..., MX:MZ + 1] = rho[..., None] * v * vn[..., None] + pt[..., None] * nvec - B * Bn[..., None]
     F[..., EN] = (U[..., EN] + pt) * vn - Bn * vB

@@ -643,6 +643,117 @@ int geo_step_adjoint(geo_mesh_t m, double dt, const double* U_in, const double* 
   return GEO_OK;
 }
 
+// ---- test support: one stage forward or reversed, on host buffers (FP64 meshes)
+static int debug_buffer_slot(geo_mesh* m, int which, void** ptr, int64_t* n) {
+  const geo::Dims& d = m->T.d;
+  const int64_t Z = m->T.Z, F = m->T.F, E = m->T.E;
+  const int nqmax = d.NQR > d.NQS ? d.NQR : d.NQS;
+  switch (which) {
+    case 0: *ptr = m->ds.Wc; *n = 8LL * d.NC1 * Z; return GEO_OK;
+    case 1: *ptr = m->ds.Bp; *n = static_cast<int64_t>(nqmax) * F; return GEO_OK;
+    case 2: *ptr = m->ds.trF; *n = static_cast<int64_t>(d.M - 1) * d.NQT * 8 * Z; return GEO_OK;
+    case 3: *ptr = m->ds.trE; *n = static_cast<int64_t>(d.M - 1) * 12 * d.NS * 8 * Z; return GEO_OK;
+    case 4: *ptr = m->ds.Ff; *n = 8 * F; return GEO_OK;
+    case 5: *ptr = m->ds.Ee; *n = E; return GEO_OK;
+    default: return fail(GEO_ERR_ARG, "unknown buffer");
+  }
+}
+
+int geo_debug_set_buffer(geo_mesh_t m, int which, const double* host, int64_t count) {
+  if (!m || !host) return fail(GEO_ERR_ARG, "bad arguments");
+  if (m->prec != GEO_FP64) return fail(GEO_ERR_ARG, "geo_debug_set_buffer: FP64 meshes only");
+  void* dst = nullptr;
+  int64_t n = 0;
+  int rc = debug_buffer_slot(m, which, &dst, &n);
+  if (rc != GEO_OK) return rc;
+  if (count != n) return fail(GEO_ERR_ARG, "geo_debug_set_buffer: count must equal the buffer size");
+  cudaError_t e = cudaMemcpyAsync(dst, host, n * sizeof(double), cudaMemcpyHostToDevice, m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "debug copy");
+  return GEO_OK;
+}
+
+int geo_debug_run_stage(geo_mesh_t m, int stage, double dt) {
+  if (!m || stage < 0 || stage >= geo::N_STAGES) return fail(GEO_ERR_ARG, "bad arguments");
+  cudaError_t e;
+  switch (m->order) {
+    case 2: e = m->prec == GEO_FP64 ? geo::launch_stage<2, double>(stage, m->dt, m->ds, dt, m->st)
+                                    : geo::launch_stage<2, float>(stage, m->dt, m->ds, dt, m->st); break;
+    case 3: e = m->prec == GEO_FP64 ? geo::launch_stage<3, double>(stage, m->dt, m->ds, dt, m->st)
+                                    : geo::launch_stage<3, float>(stage, m->dt, m->ds, dt, m->st); break;
+    default: e = m->prec == GEO_FP64 ? geo::launch_stage<4, double>(stage, m->dt, m->ds, dt, m->st)
+                                     : geo::launch_stage<4, float>(stage, m->dt, m->ds, dt, m->st); break;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return cuda_fail(e, "geo_debug_run_stage");
+  return GEO_OK;
+}
+
+int geo_debug_stage_vjp(geo_mesh_t m, int stage, double dt, const double* U, const double* phi, const double* g_out,
+                        int64_t n_out, double* g_in, int64_t n_in) {
+  if (!m || !U || !phi || !g_out || !g_in || !(dt > 0.0)) return fail(GEO_ERR_ARG, "bad arguments");
+  if (m->prec != GEO_FP64) return fail(GEO_ERR_ARG, "geo_debug_stage_vjp: FP64 meshes only");
+  int rc = ensure_adjoint_buffers(m);
+  if (rc != GEO_OK) return rc;
+  const geo::Dims& d = m->T.d;
+  const size_t Z = m->T.Z, F = m->T.F, E = m->T.E;
+  const int64_t nW = 8LL * d.NC1 * Z, nF = static_cast<int64_t>(d.M - 1) * d.NQT * 8 * Z,
+                nE = static_cast<int64_t>(d.M - 1) * 12 * d.NS * 8 * Z;
+  geo::AdjState A = m->adj;
+  double *dst_out = nullptr, *src_in = nullptr;
+  int64_t want_out = 0, want_in = 0;
+  switch (stage) {
+    case geo::ST_WENO: dst_out = A.gW; want_out = nW; want_in = 8 * Z; break;
+    case geo::ST_ADER: dst_out = A.gtrF; want_out = nF + nE; src_in = A.gW; want_in = nW; break;
+    case geo::ST_FACE: dst_out = A.gFf; want_out = 8 * F; src_in = A.gtrF; want_in = nF; break;
+    case geo::ST_EDGE: dst_out = A.gEe; want_out = E; src_in = A.gtrE; want_in = nE; break;
+    default: return fail(GEO_ERR_ARG, "geo_debug_stage_vjp: stage must be WENO, ADER, FACE or EDGE");
+  }
+  if (n_out != want_out || n_in != want_in) return fail(GEO_ERR_ARG, "geo_debug_stage_vjp: wrong buffer sizes");
+  // the zone cotangents: a zero incoming one, and the WENO stage's output
+  double* gU0 = nullptr;
+  double* gU = nullptr;
+  cudaError_t e = cudaMalloc(&gU0, 8 * Z * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&gU, 8 * Z * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(gU0, 0, 8 * Z * sizeof(double), m->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gU, 0, 8 * Z * sizeof(double), m->st);
+  // forward intermediates of (U, phi), as in geo_step_adjoint
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_U0, U, 8 * Z * sizeof(double), cudaMemcpyHostToDevice, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_fwd.U, U, 8 * Z * sizeof(double), cudaMemcpyHostToDevice, m->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_fwd.phi, phi, F * sizeof(double), cudaMemcpyHostToDevice, m->st);
+  for (int s = geo::ST_WENO; s <= geo::ST_ADER && e == cudaSuccess; ++s) {
+    switch (m->order) {
+      case 2: e = geo::launch_stage<2, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
+      case 3: e = geo::launch_stage<3, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
+      default: e = geo::launch_stage<4, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
+    }
+  }
+  A.gUp = gU0;
+  A.gphip = nullptr;
+  A.gU = gU;
+  if (stage == geo::ST_ADER) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.gtrF, g_out, nF * sizeof(double), cudaMemcpyHostToDevice, m->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.gtrE, g_out + nF, nE * sizeof(double), cudaMemcpyHostToDevice, m->st);
+  } else if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(dst_out, g_out, want_out * sizeof(double), cudaMemcpyHostToDevice, m->st);
+  }
+  if (e == cudaSuccess) {
+    switch (m->order) {
+      case 2: e = geo::launch_adjoint_stage<2>(stage, m->dt, m->adj_fwd, A, dt, m->st); break;
+      case 3: e = geo::launch_adjoint_stage<3>(stage, m->dt, m->adj_fwd, A, dt, m->st); break;
+      default: e = geo::launch_adjoint_stage<4>(stage, m->dt, m->adj_fwd, A, dt, m->st); break;
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g_in, stage == geo::ST_WENO ? gU : src_in, want_in * sizeof(double), cudaMemcpyDeviceToHost,
+                        m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  cudaFree(gU0);
+  cudaFree(gU);
+  if (e != cudaSuccess) return cuda_fail(e, "geo_debug_stage_vjp");
+  return GEO_OK;
+}
+
 int geo_outer_Br2(geo_mesh_t m, const double* phi_dev, double* J, double* gphi_dev) {
   if (!m || !phi_dev || !J) return fail(GEO_ERR_ARG, "geo_outer_Br2: bad arguments");
   cudaError_t e = cudaSuccess;

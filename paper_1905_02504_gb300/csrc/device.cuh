@@ -129,6 +129,10 @@ cudaError_t probe_fma(int prec, cudaStream_t st, double* flops_per_s);
 // state are in S (Wc, Bp, trF, trE), the pristine checkpoint in A.U0
 template <int P>
 cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState& A, double dt, cudaStream_t st);
+// the reverse kernel of one forward stage alone (ST_WENO, ST_ADER, ST_FACE, ST_EDGE)
+template <int P>
+cudaError_t launch_adjoint_stage(int stage, const DevTables& T, const DevState& S, const AdjState& A, double dt,
+                                 cudaStream_t st);
 int reduction_blocks(long long n);
 cudaError_t launch_outer_br2(const DevTables& T, const double* phi, double* out_dev, double* gphi, cudaStream_t st);
 

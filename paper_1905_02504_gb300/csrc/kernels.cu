@@ -1557,6 +1557,26 @@ cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState
   k_adj_weno<P><<<grid_for(T.Z), TPB, 0, st>>>(T, A);
   return cudaGetLastError();
 }
+template <int P>
+cudaError_t launch_adjoint_stage(int stage, const DevTables& T, const DevState& S, const AdjState& A, double dt,
+                                 cudaStream_t st) {
+  const double* Wc = static_cast<const double*>(S.Wc);
+  const double* Bp = static_cast<const double*>(S.Bp);
+  switch (stage) {
+    case ST_WENO: k_adj_weno<P><<<grid_for(T.Z), TPB, 0, st>>>(T, A); break;
+    case ST_ADER: k_adj_ader<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.phi, Wc, Bp, A, dt); break;
+    case ST_FACE: k_adj_face<P><<<grid_for(T.F), TPB, 0, st>>>(T, static_cast<const double*>(S.trF), A, dt); break;
+    case ST_EDGE: k_adj_edge<P><<<grid_for(T.E), TPB, 0, st>>>(T, static_cast<const double*>(S.trE), A, dt); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_adjoint_stage<2>(int, const DevTables&, const DevState&, const AdjState&, double,
+                                             cudaStream_t);
+template cudaError_t launch_adjoint_stage<3>(int, const DevTables&, const DevState&, const AdjState&, double,
+                                             cudaStream_t);
+template cudaError_t launch_adjoint_stage<4>(int, const DevTables&, const DevState&, const AdjState&, double,
+                                             cudaStream_t);
 template cudaError_t launch_adjoint<2>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
 template cudaError_t launch_adjoint<3>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);
 template cudaError_t launch_adjoint<4>(const DevTables&, const DevState&, const AdjState&, double, cudaStream_t);

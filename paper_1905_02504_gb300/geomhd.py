@@ -60,6 +60,9 @@ _SIGS = {
     "geo_stage_flops": [_h, _vp, _vp],
     "geo_probe_fma_peak": [ctypes.c_int, _vp, _pd],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
+    "geo_debug_set_buffer": [_h, ctypes.c_int, _vp, _i64],
+    "geo_debug_run_stage": [_h, ctypes.c_int, _d],
+    "geo_debug_stage_vjp": [_h, ctypes.c_int, _d, _vp, _vp, _vp, _i64, _vp, _i64],
     "geo_cfl_dt_noalloc": [_h, _vp, _d, _vp],
     "geo_step_adjoint": [_h, _d, _vp, _vp, _vp, _vp, _vp, _vp],
     "geo_outer_Br2": [_h, _vp, _pd, _vp],
@@ -246,6 +249,25 @@ def geo_debug_buffer(h, which, count):
     out = np.empty(count)
     _check(_lib.geo_debug_buffer(h, which, _ptr(out), count), "geo_debug_buffer")
     return out
+
+
+def geo_debug_set_buffer(h, which, data):
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    _check(_lib.geo_debug_set_buffer(h, int(which), _ptr(data), data.size), "geo_debug_set_buffer")
+
+
+def geo_debug_run_stage(h, stage, dt):
+    _check(_lib.geo_debug_run_stage(h, int(stage), float(dt)), "geo_debug_run_stage")
+
+
+def geo_debug_stage_vjp(h, stage, dt, U, phi, g_out, n_in):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    g_out = np.ascontiguousarray(g_out, dtype=np.float64)
+    g_in = np.empty(n_in)
+    _check(_lib.geo_debug_stage_vjp(h, int(stage), float(dt), _ptr(U), _ptr(phi), _ptr(g_out), g_out.size,
+                                    _ptr(g_in), n_in), "geo_debug_stage_vjp")
+    return g_in
 
 
 def geo_cfl_dt_noalloc(h, U_dev, cfl, dt_dev):
