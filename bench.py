@@ -281,19 +281,39 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
-def captured_traffic(a, kernel, Z, prec="fp64"):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu capture
-    (a smaller case of the same kernel), scaled by zones; None when the kernel
-    source changed since the capture."""
+PREDICTOR_SOURCES = ("device.cuh", "mhd_device.cuh", "ader_vt.cuh")
+
+
+def predictor_fingerprint():
+    """sha256 prefix of the predictor kernels' source: the node-team section of
+    kernels.cu (from the team sizes to the face-flux stage), ader_vt.cuh and the
+    device headers they use.  Edits elsewhere in the library leave it unchanged."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_1905_02504_gb300", "csrc")
+    k = open(os.path.join(csrc, "kernels.cu")).read()
+    a = k.index("template <int P> struct Team;")
+    b = k.index("// a4: face fluxes")
+    h = hashlib.sha256(k[a:b].encode())
+    for f in PREDICTOR_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(a, kernel, Z, prec="fp64"):
+    """DRAM bytes of one launch of the dominant kernel: the DRAM bytes per zone of
+    the committed ncu capture of the same kernel, order and form
+    (profiles/k_ader_traffic.json; captured on a 196,608-zone case, the traffic
+    growing in proportion to the zones) times the zones of this launch; None when
+    there is no such capture or the predictor source changed since."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_1905_02504_gb300", "csrc", "kernels.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["kernels_cu_sha256_prefix"] or rec["order"] != a.order:
-            return None
-        return rec["dram_bytes_per_zone"][prec] * Z
+        recs = json.load(open(os.path.join(ROOT, "profiles", "k_ader_traffic.json")))["records"]
+        fp = predictor_fingerprint()
+        for r in recs:
+            if (r["kernel"], r["order"], r["form"], r["source_fingerprint"]) == (kernel, a.order, prec, fp):
+                return r["dram_bytes_per_zone"] * Z
     except (OSError, KeyError, ValueError):
-        return None
+        pass
+    return None
 
 
 def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
@@ -352,7 +372,8 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "ms_per_step": t_ms / a.steps, "dtype": "f32 bulk / f64 accumulation and updates",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": achieved / nominal_fp32,
-                     "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], m32.Z, "fp32"),
+                     "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), m32.Z,
+                                                "fp32"),
                      "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity),
                      "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
                                   "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
@@ -501,7 +522,8 @@ def gpu_arm(a):
         kind = "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak
     roofline = {"bound": "alu", "achieved": achieved, "peak": nominal, "unit": "TFLOP/s",
                 "frac": achieved / nominal,
-                "traffic": captured_traffic(a, "k_" + geomhd.STAGES[top], Z, "fp32" if a.fp32_only else "fp64"),
+                "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), Z,
+                                            "fp32" if a.fp32_only else "fp64"),
                 "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), "peak_kind": kind, "measured_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}

@@ -111,11 +111,20 @@ __device__ __forceinline__ void vt_contract(const R* XFz, R* XOz, int v, const R
 }
 
 template <int P, typename R, int G = 0>
-__device__ __forceinline__ void vt_contract_group(int g, const R* XFz, R* XOz, int v, const RefConst<P, R>& K) {
+__device__ __forceinline__ void vt_contract_dispatch(int g, const R* XFz, R* XOz, int v, const RefConst<P, R>& K) {
   if constexpr (G < RefPattern<P>::G) {
     if (g == G) vt_contract<P, R, G>(XFz, XOz, v, K);
-    else vt_contract_group<P, R, G + 1>(g, XFz, XOz, v, K);
+    else vt_contract_dispatch<P, R, G + 1>(g, XFz, XOz, v, K);
   }
+}
+
+// One out-of-line copy of the variable phase for all groups: the predictor calls
+// it from 1 + (M-1) places (level 1, then each level inside the Picard loop), and
+// inlining it there multiplied the fully unrolled group code M-fold, beyond what
+// the instruction cache holds.
+template <int P, typename R>
+__device__ __noinline__ void vt_contract_group(int g, const R* XFz, R* XOz, int v) {
+  vt_contract_dispatch<P, R>(g, XFz, XOz, v, RC<P, R>::get());
 }
 
 // ---- point evaluations: the (M-1) x (NQT + 12 NS) points of a zone, level-major,
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, VtOcc<P, R>::MINB)
       }
     }
     __syncthreads();
-    if (vrole) vt_contract_group<P, R>(vg, XFv, XOv, vv, K);
+    if (vrole) vt_contract_group<P, R>(vg, XFv, XOv, vv);
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < 8; ++v) dFm[v] += XOz[v * N + i];

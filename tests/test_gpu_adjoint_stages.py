@@ -11,9 +11,10 @@ stage's reverse kernel alone.
   faces      x = face-point states          y = time-integrated HLL face fluxes
   edges      x = edge-point states          y = time-integrated edge EMFs
 
-The base state carries 10 % seeded noise (as in the full-step checks), so the
+The base state carries 10 % seeded noise (as in the full-step checks), so most
 MinMod / HLL / Rusanov and |beta_H - beta_k| decisions sit far from their
-switches compared with the +-2h stencil."""
+switches compared with the +-2h stencil; a direction whose differences at h and
+h/4 disagree crossed a switch and is skipped (at least two of four must count)."""
 import numpy as np
 import pytest
 
@@ -82,16 +83,23 @@ def test_stage_transpose(n, nr, p, stage):
     fixed["Bp"] = g.geo_debug_buffer(mesh.h, 1, nqmax * mesh.F)
     x0 = base[stage]
     y0 = forward_stage(mesh, stage, dt, U, phi, x0, fixed)
-    for trial in range(3):
+    checked = 0
+    for trial in range(4):
         w = rng.standard_normal(y0.size)
         d = rng.uniform(-1.0, 1.0, x0.size) * np.maximum(np.abs(x0), 1e-3 * np.abs(x0).max())
-        h = H
 
-        def J(xx):
-            return float(w @ forward_stage(mesh, stage, dt, U, phi, xx, fixed))
+        def fd(h):
+            # difference the stage outputs first, then project: a projection of
+            # ~1e4 terms before differencing would leave ~1e-7 relative rounding
+            f = lambda t: forward_stage(mesh, stage, dt, U, phi, x0 + t * d, fixed)
+            return float(w @ ((8.0 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12.0 * h)))
 
-        fd = (8.0 * (J(x0 + h * d) - J(x0 - h * d)) - (J(x0 + 2 * h * d) - J(x0 - 2 * h * d))) / (12.0 * h)
+        f1, f2 = fd(H), fd(H / 4)
+        if abs(f1 - f2) > 1e-8 * abs(f2):
+            continue        # a MinMod / HLL / Rusanov switch inside the stencil: a secant, not a derivative
         gx = g.geo_debug_stage_vjp(mesh.h, stage, dt, U, phi, w, x0.size)
         adj = float(gx @ d)
-        assert abs(adj - fd) <= TOL * abs(fd), (trial, adj, fd)
+        assert abs(adj - f2) <= TOL * abs(f2), (trial, adj, f1, f2)
+        checked += 1
+    assert checked >= 2, checked
     mesh.close()
