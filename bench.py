@@ -53,6 +53,7 @@ def parse():
                     help="workload; the spherical shock tubes use their own shells (inputs.DOMAINS)")
     ap.add_argument("--noise", type=float, default=0.0, help="seeded relative density noise")
     ap.add_argument("--positivity", action="store_true")
+    ap.add_argument("--riemann", default="hll", choices=["hll", "hlld"], help="face Riemann solver")
     ap.add_argument("--fp32-only", action="store_true", help="time only the FP32-bulk form")
     ap.add_argument("--cfl-every-step", action="store_true",
                     help="device CFL reduction before every timed step (dt read back each step)")
@@ -85,6 +86,8 @@ def workload_name(a):
         extra += ", density noise %g" % a.noise
     if getattr(a, "cfl_every_step", False):
         extra += ", device CFL every step"
+    if getattr(a, "riemann", "hll") == "hlld":
+        extra += ", HLLD faces"
     return "cubed-sphere %dx%dx%d x %d shells (%d zones), order %d, %s, %s test%s" % (
         6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order, form, getattr(a, "problem", "smooth"), extra)
 
@@ -332,6 +335,8 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         geomhd.geo_set_predictor(m32.h, a.predictor)
     if a.positivity:
         geomhd.geo_set_positivity(m32.h, 1)
+    if a.riemann == "hlld":
+        geomhd.geo_set_riemann(m32.h, geomhd.GEO_RIEMANN_HLLD)
     m32.upload(U0, phi0)
     with torch.cuda.stream(stream):
         for _ in range(a.warmup):
@@ -449,6 +454,8 @@ def gpu_arm(a):
         geomhd.geo_set_predictor(mesh.h, a.predictor)
     if a.positivity:
         geomhd.geo_set_positivity(mesh.h, 1)
+    if a.riemann == "hlld":
+        geomhd.geo_set_riemann(mesh.h, geomhd.GEO_RIEMANN_HLLD)
     U0, phi0 = mesh.initial_state(make_problem(a.problem, noise=a.noise), nq_zone=a.nq_zone or None,
                                   nq_edge=a.nq_edge)
     mesh.upload(U0, phi0)

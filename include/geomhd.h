@@ -97,6 +97,18 @@ int geo_set_gamma(geo_mesh_t mesh, double gamma);
  * type scaling; the pressure bound uses the concavity of p).  Default: off. */
 int geo_set_positivity(geo_mesh_t mesh, int enable);
 
+/* Face Riemann solver of the corrector (Sec. VI step 5; the paper does not name
+ * its solver and points to higher-fidelity ones in Sec. I):
+ *   GEO_RIEMANN_HLL  (0, default): HLL with Davis wave speeds;
+ *   GEO_RIEMANN_HLLD (1): HLLD (Miyoshi & Kusano 2005): fast, Alfven and entropy
+ *     waves, exact for isolated contacts and rotational discontinuities; the
+ *     normal field at a face point is the mean of its two sides'.
+ * The edge EMFs keep the multidimensional Rusanov solver.  geo_step_adjoint
+ * refuses a mesh set to HLLD (GEO_ERR_ARG).  Returns GEO_ERR_ARG for any other
+ * value. */
+enum { GEO_RIEMANN_HLL = 0, GEO_RIEMANN_HLLD = 1 };
+int geo_set_riemann(geo_mesh_t mesh, int solver);
+
 /* Execution schedule of the predictor stage (a2 zone part + a3, Sec. IV.b steps
  * 8-10 and Eqs. C.34-C.36); all compute the same arithmetic:
  *   GEO_PRED_ZONE_THREAD (0): one thread per zone, its nodal states in

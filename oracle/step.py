@@ -8,6 +8,8 @@ Phi (F,):
   3. ADER-CG predictor (ader.py).
   4. Corrector:
      * face flux  F_f = dt sum_{m>=2} w_m sum_q w_q |dA_q| HLL(U_L, U_R; n_q)
+       (or HLLD, riemann="hlld": the higher-fidelity face solver of the paper's
+       introduction)
        at every face quadrature point and Gauss time (the space and time
        integrals switch places, Sec. V.d step 10);
      * edge EMF   E_e = dt sum_{m>=2} w_m sum_s w_s |dl_s| (E.t)_s with the
@@ -36,14 +38,16 @@ from . import positivity, quadrature
 from .ader import AderPredictor
 from .divfree import DivFreeB
 from .mesh import Mesh
-from .physics import edge_emf, hll, primitives, rusanov_speed, fast_speed
+from .physics import edge_emf, hll, hlld, primitives, rusanov_speed, fast_speed
 from .weno import WenoAO
 
 
 class Oracle:
-    def __init__(self, n, nr, r_in, r_out, p, gamma=5.0 / 3.0, positivity=False):
+    def __init__(self, n, nr, r_in, r_out, p, gamma=5.0 / 3.0, positivity=False, riemann="hll"):
         self.gamma = gamma
         self.positivity = positivity
+        assert riemann in ("hll", "hlld")
+        self.riemann = hlld if riemann == "hlld" else hll
         m = self.mesh = Mesh(n, nr, r_in, r_out, p)
         self.weno = WenoAO(m)
         self.dfb = DivFreeB(m, self.weno)
@@ -191,7 +195,7 @@ class Oracle:
                     sR = sL
                 if sL is None:
                     sL = sR
-                Fq = hll(sL, sR, n, g)
+                Fq = self.riemann(sL, sR, n, g)
                 Fface[f] += dt * self.wt[mi - 1] * (W[:, None] * Fq).sum(0)
         # ---- edge EMFs
         Eedge = np.zeros(m.E)

@@ -172,6 +172,7 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.gamma = 5.0 / 3.0;
   D.positivity = 0;
   D.predictor = GEO_PRED_NODE_TEAM;
+  D.riemann = GEO_RIEMANN_HLL;
   std::vector<double> qpow(T.nr + 2);
   for (int k = 0; k < T.nr + 2; ++k) qpow[k] = std::pow(T.q, k);
   D.qpow = m->upload(qpow, err);
@@ -347,6 +348,13 @@ int geo_set_gamma(geo_mesh_t m, double gamma) {
 int geo_set_positivity(geo_mesh_t m, int enable) {
   if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
   m->dt.positivity = enable ? 1 : 0;
+  return GEO_OK;
+}
+
+int geo_set_riemann(geo_mesh_t m, int solver) {
+  if (!m) return fail(GEO_ERR_ARG, "mesh is NULL");
+  if (solver != GEO_RIEMANN_HLL && solver != GEO_RIEMANN_HLLD) return fail(GEO_ERR_ARG, "unknown face solver");
+  m->dt.riemann = solver;
   return GEO_OK;
 }
 
@@ -610,6 +618,8 @@ int geo_step_adjoint(geo_mesh_t m, double dt, const double* U_in, const double* 
   if (m->prec != GEO_FP64) return fail(GEO_ERR_ARG, "geo_step_adjoint: the adjoint is available for GEO_FP64 meshes");
   if (m->dt.positivity)
     return fail(GEO_ERR_ARG, "geo_step_adjoint: the positivity scaling is not differentiated; switch it off");
+  if (m->dt.riemann != GEO_RIEMANN_HLL)
+    return fail(GEO_ERR_ARG, "geo_step_adjoint: the reverse sweep differentiates the HLL face solver only");
   int rc = ensure_adjoint_buffers(m);
   if (rc != GEO_OK) return rc;
   const size_t Z = m->T.Z, F = m->T.F;

@@ -58,7 +58,8 @@ struct DevTables {
   long long Z, F, E, F_rad, E_rad;
   double gamma;
   int positivity;      // 1: scale nodal and point states toward the zone mean (rho, p > 0)
-  int predictor;       // 0: one thread per zone; 1: a team of N threads per zone (one per node)
+  int predictor;       // GEO_PRED_*: the predictor's execution schedule
+  int riemann;         // GEO_RIEMANN_*: the face solver
   int* status;         // [1] bit 0 set by the U update when a zone leaves rho > 0, p > 0 (or is not finite)
   const double* qpow;  // [nr + 2]: q^k
   const double* iA0;   // [ncol][6]: 1 / A0 (reciprocal face areas at shell 0)

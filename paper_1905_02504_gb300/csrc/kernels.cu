@@ -987,7 +987,7 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
 // ----------------------------------------------------------------------------
 // a4: face fluxes (HLL at face points x Gauss times, FP64 accumulation)
 // ----------------------------------------------------------------------------
-template <int P, typename R>
+template <int P, typename R, bool HLLD>
 __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* __restrict__ trF,
                                                    double* __restrict__ Ff, double dt) {
   using Dm = Dim<P>;
@@ -1036,7 +1036,8 @@ __global__ void __launch_bounds__(TPB) k_face_flux(const DevTables T, const R* _
 #pragma unroll
         for (int v = 0; v < 8; ++v) uR[v] = uL[v];
       }
-      hll_acc(uL, uR, nx, ny, nz, g, W, acc);
+      if constexpr (HLLD) hlld_acc(uL, uR, nx, ny, nz, g, W, acc);
+      else hll_acc(uL, uR, nx, ny, nz, g, W, acc);
     }
   }
 #pragma unroll
@@ -1515,7 +1516,10 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
       }
       break;
     case ST_FACE:
-      k_face_flux<P, R><<<grid_for(T.F), TPB, 0, st>>>(T, trF, S.Ff, dt);
+      if (T.riemann == GEO_RIEMANN_HLLD)
+        k_face_flux<P, R, true><<<grid_for(T.F), TPB, 0, st>>>(T, trF, S.Ff, dt);
+      else
+        k_face_flux<P, R, false><<<grid_for(T.F), TPB, 0, st>>>(T, trF, S.Ff, dt);
       break;
     case ST_EDGE:
       k_edge_emf<P, R><<<grid_for(T.E), TPB, 0, st>>>(T, trE, S.Ee, dt);

@@ -43,6 +43,7 @@ _SIGS = {
     "geo_set_gamma": [_h, _d],
     "geo_set_positivity": [_h, ctypes.c_int],
     "geo_set_predictor": [_h, ctypes.c_int],
+    "geo_set_riemann": [_h, ctypes.c_int],
     "geo_check_state": [_h, ctypes.POINTER(ctypes.c_int)],
     "geo_zone_cubature": [_h, ctypes.c_int, _vp, _vp],
     "geo_edge_quadrature": [_h, ctypes.c_int, _vp, _vp],
@@ -130,6 +131,12 @@ def geo_set_positivity(h, enable):
 GEO_PRED_ZONE_THREAD = 0
 GEO_PRED_NODE_TEAM = 1
 GEO_PRED_VAR_TEAM = 2
+GEO_RIEMANN_HLL = 0
+GEO_RIEMANN_HLLD = 1
+
+
+def geo_set_riemann(h, solver):
+    _check(_lib.geo_set_riemann(h, int(solver)), "geo_set_riemann")
 
 
 def geo_set_predictor(h, schedule):

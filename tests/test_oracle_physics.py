@@ -1,5 +1,6 @@
 """Pins of the oracle's fluxes and Riemann solvers (Eq. 2.2; readings of Sec. VI)."""
 import numpy as np
+import pytest
 
 from oracle import physics as ph
 
@@ -89,3 +90,75 @@ def test_edge_emf_reduces_to_1d_rusanov():
     FE = ph.flux_dir(UE, x, G)[6]
     rus = 0.5 * (FW + FE) - 0.5 * a * (UE[6] - UW[6])
     assert abs(E - (-rus)) < 1e-13
+
+
+# ---------------------------------------------------------------- HLLD
+def _state(rho, v, p, B, g=5.0 / 3.0):
+    from oracle.physics import conserved
+    return conserved(np.array(rho), np.array(v, dtype=float), np.array(p), np.array(B, dtype=float), g)
+
+
+def test_hlld_consistency_and_supersonic_upwinding():
+    """Identical states give the physical flux; a supersonic flow gives the
+    upwind flux (Miyoshi & Kusano 2005, consistency and upwinding)."""
+    from oracle.physics import flux_dir, hlld
+    g = 5.0 / 3.0
+    n = np.array([0.6, 0.0, 0.8])
+    U = _state(1.2, [0.3, -0.2, 0.1], 0.9, [0.4, 0.5, -0.3])
+    assert np.abs(hlld(U, U, n, g) - flux_dir(U, n, g)).max() < 1e-15
+    UL = _state(1.0, 8.0 * n, 0.5, [0.2, 0.1, 0.0])
+    UR = _state(0.5, 7.0 * n, 0.3, [0.1, 0.3, -0.2])
+    # upwinding: the left state with the mean normal field
+    ex = _state(1.0, 8.0 * n, 0.5, [0.2, 0.1, 0.0] + (0.5 * (0.12 + (0.06 - 0.16)) - 0.12) * n)
+    assert np.abs(hlld(UL, UR, n, g) - flux_dir(ex, n, g)).max() < 1e-13
+
+
+def test_hlld_rotation_invariance():
+    from oracle.physics import hlld
+    g = 5.0 / 3.0
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    n = np.array([0.0, 0.6, 0.8])
+    UL = _state(1.0, [0.2, -0.1, 0.3], 1.0, [0.5, 0.3, -0.4])
+    UR = _state(0.3, [-0.4, 0.2, 0.0], 0.2, [0.1, -0.6, 0.2])
+
+    def rot(U):
+        V = U.copy()
+        V[1:4] = Q @ U[1:4]
+        V[5:8] = Q @ U[5:8]
+        return V
+
+    a = hlld(rot(UL), rot(UR), Q @ n, g)
+    b = rot(hlld(UL, UR, n, g))
+    assert np.abs(a - b).max() < 1e-13
+
+
+@pytest.mark.parametrize("Bn", [0.0, 0.7])
+def test_hlld_resolves_a_stationary_contact(Bn):
+    """A stationary contact (density jump, equal pressure, continuous tangential
+    v and B) carries no mass: the HLLD flux is the exact flux, while HLL
+    diffuses it."""
+    from oracle.physics import flux_dir, hll, hlld
+    g = 5.0 / 3.0
+    n = np.array([1.0, 0.0, 0.0])
+    UL = _state(1.0, [0.0, 0.3, 0.1], 1.0, [Bn, 0.5, 0.2])
+    UR = _state(0.2, [0.0, 0.3, 0.1], 1.0, [Bn, 0.5, 0.2])
+    assert np.abs(hlld(UL, UR, n, g) - flux_dir(UL, n, g)).max() < 1e-14
+    assert abs(hll(UL, UR, n, g)[0]) > 0.1
+
+
+@pytest.mark.parametrize("sgn", [1.0, -1.0])
+def test_hlld_resolves_an_isolated_alfven_discontinuity(sgn):
+    """A rotational discontinuity: equal rho, p, B_n and |B_t|, tangential field
+    rotated and [v_t] = sgn [B_t] / sqrt(rho).  With sgn = -1 (B_n > 0) it moves
+    to the right, and the flux at the interface is the left state's; with sgn = +1
+    it moves left and the flux is the right state's.  HLLD returns either exactly."""
+    from oracle.physics import flux_dir, hlld
+    g = 5.0 / 3.0
+    n = np.array([1.0, 0.0, 0.0])
+    BtL, BtR, vtL = np.array([0.6, 0.0]), np.array([0.0, 0.6]), np.array([0.1, -0.2])
+    vtR = vtL + sgn * (BtR - BtL)
+    UL = _state(1.0, [0.0, *vtL], 1.0, [0.8, *BtL])
+    UR = _state(1.0, [0.0, *vtR], 1.0, [0.8, *BtR])
+    up = UL if sgn < 0 else UR
+    assert np.abs(hlld(UL, UR, n, g) - flux_dir(up, n, g)).max() < 1e-14

@@ -206,3 +206,26 @@ def test_shock_tube_initial_field_divergence_free(name):
     assert np.abs(rad - rad[:, :1]).max() < 1e-13 * np.abs(rad).max()
     assert np.abs(rad).max() > 0.1
     assert np.array_equal(phi[m.ncol * (m.nr + 1):], phi_a[m.ncol * (m.nr + 1):])
+
+
+def test_hlld_step_free_stream_divb_and_ledger():
+    """The step with the HLLD face solver keeps the full-step invariants: a
+    uniform state stays uniform, div B stays at rounding, and mass and energy
+    change by exactly the boundary-flux ledger."""
+    o = Oracle(3, 3, 1.0, 2.0, 2, riemann="hlld")
+    U, phi = o.initial_state(make_problem("uniform", v0=(0.4, -0.3, 0.2), B0=(0.3, -0.2, 0.5)))
+    dt = o.cfl_dt(U, 0.3)
+    U1, phi1 = o.step(U, phi, dt)
+    assert (np.abs(U1 - U).max(0) / np.abs(U).max(0)).max() < 1e-14
+    U, phi = o.initial_state(make_problem("blast"))
+    dt = o.cfl_dt(U, 0.4)
+    m = o.mesh
+    U1, phi1, st = o.step(U, phi, dt, return_stages=True)
+    F = st["Fface"]
+    inner = np.arange(m.ncol) * (m.nr + 1)
+    ledger = F[inner].sum(0) - F[inner + m.nr].sum(0)
+    Ustart = U.copy()
+    Ustart[:, 5:8] = st["Bmean"]
+    change = (o.V[:, None] * (U1 - Ustart)).sum(0)
+    assert (np.abs(change - ledger) / (o.V[:, None] * np.abs(U1)).sum(0)).max() < 1e-13
+    assert o.divB(phi1)[1] < 1e-13
