@@ -14,8 +14,8 @@
 //                   the D values are constant-bank operands, and the only shared
 //                   traffic is one 16-byte load per needed 4-node chunk of F.
 // The final levels are exchanged once more the same way, and each (zone, v,
-// group) thread evaluates its share of the face and edge points (the supports
-// and the node lists are compiled in as well) and writes the traces.
+// group) thread evaluates its share of the face and edge points (face by face,
+// edge by edge: the support node lists are compiled in) and writes the traces.
 // Groups are balanced by entry (point) count; the group index is the slowest
 // part of the thread index, so every warp runs the code of one group.
 // Only the unlimited predictor has this schedule: with positivity on, the
@@ -127,86 +127,93 @@ __device__ __noinline__ void vt_contract_group(int g, const R* XFz, R* XOz, int 
   vt_contract_dispatch<P, R>(g, XFz, XOz, v, RC<P, R>::get());
 }
 
-// ---- point evaluations: the (M-1) x (NQT + 12 NS) points of a zone, level-major,
-// face points before edge points within a level; cost = the support size
+// ---- point evaluations.  Work items are (level m, face or edge e), level-major,
+// the 6 faces before the 12 edges; an item's points share its support nodes
+// (the face's / edge's nodes), so a thread loads those values once (compile-time
+// node indices) and loops over the item's points at run time, the basis weights
+// coming from constant memory (the same address for the whole warp).  Items go to
+// the row groups in contiguous ranges balanced by cost (points x support).
 template <int P>
-struct VtPoints {
+struct VtItems {
   using Dm = Dim<P>;
   using RP = RefPattern<P>;
-  static constexpr int NPL = Dm::NQT + 12 * Dm::NS, NPT = (Dm::M - 1) * NPL, G = RP::G;
-  __host__ __device__ static constexpr int cost(int t) { return (t % NPL) < Dm::NQT ? RP::NFN : RP::NEN; }
+  static constexpr int NE = 18, NIT = (Dm::M - 1) * NE, G = RP::G;
+  __host__ __device__ static constexpr int np(int e) { return e < 4 ? Dm::NQS : (e < 6 ? Dm::NQR : Dm::NS); }
+  __host__ __device__ static constexpr int cost(int t) {
+    return np(t % NE) * ((t % NE) < 6 ? RP::NFN : RP::NEN);
+  }
   __host__ __device__ static constexpr int total() {
     int s = 0;
-    for (int t = 0; t < NPT; ++t) s += cost(t);
+    for (int t = 0; t < NIT; ++t) s += cost(t);
     return s;
   }
-  // first point of group g (balanced by cost)
+  // first item of group g
   __host__ __device__ static constexpr int start(int g) {
     if (g <= 0) return 0;
-    if (g >= G) return NPT;
+    if (g >= G) return NIT;
     int s = 0;
-    for (int t = 0; t < NPT; ++t) {
+    for (int t = 0; t < NIT; ++t) {
       if (s * G >= total() * g) return t;
       s += cost(t);
     }
-    return NPT;
+    return NIT;
   }
-  __host__ __device__ static constexpr int face_of(int idx) {
-    return idx < 4 * Dm::NQS ? idx / Dm::NQS : 4 + (idx - 4 * Dm::NQS) / Dm::NQR;
+  // first face point of local face lf (faces 0-3: NQS points, 4-5: NQR)
+  __host__ __device__ static constexpr int foff(int lf) {
+    return lf < 4 ? lf * Dm::NQS : 4 * Dm::NQS + (lf - 4) * Dm::NQR;
   }
 };
 
-template <int P, typename R, int T0, int... As>
-__device__ __forceinline__ R vt_face_point(const R* Xr, const RefConst<P, R>& K, std::integer_sequence<int, As...>) {
+template <int P, typename R, int S0, int... As>
+__device__ __forceinline__ void vt_gather(const R* row, R* Xs, std::integer_sequence<int, As...>) {
   using RP = RefPattern<P>;
-  using PT = VtPoints<P>;
-  constexpr int idx = T0 % PT::NPL, lf = PT::face_of(idx);
-  return ((K.psiFc[idx * RP::NFN + As] * Xr[IC<RP::FN[lf * RP::NFN + As]>::value]) + ...);
+  ((Xs[As] = row[IC<S0 < 6 * RP::NFN ? RP::FN[S0 + As] : RP::EN[S0 - 6 * RP::NFN + As]>::value]), ...);
 }
 
-template <int P, typename R, int T0, int... As>
-__device__ __forceinline__ R vt_edge_point(const R* Xr, const RefConst<P, R>& K, std::integer_sequence<int, As...>) {
+// one item T = m * 18 + e of variable v
+template <int P, typename R, int T>
+__device__ __forceinline__ void vt_item(const R* XFz, int v, const RefConst<P, R>& K, const R* iJF, const R* iJE,
+                                        R* trF, R* trE, long long Z, long long z, bool valid) {
+  using IT = VtItems<P>;
   using RP = RefPattern<P>;
-  using PT = VtPoints<P>;
-  constexpr int idx = T0 % PT::NPL - Dim<P>::NQT, le = idx / Dim<P>::NS;
-  return ((K.psiEc[idx * RP::NEN + As] * Xr[IC<RP::EN[le * RP::NEN + As]>::value]) + ...);
-}
-
-// the points [T0, T1) of one level m, from that level's values Xr of variable v
-template <int P, typename R, int T0, int T1>
-__device__ __forceinline__ void vt_points(const R* Xr, int v, const RefConst<P, R>& K, const R* iJF, const R* iJE,
-                                          R* trF, R* trE, long long Z, long long z, bool valid) {
-  if constexpr (T0 < T1) {
-    using PT = VtPoints<P>;
-    using Dm = Dim<P>;
-    constexpr int m = T0 / PT::NPL, r = T0 % PT::NPL;
-    if constexpr (r < Dm::NQT) {
-      R s = vt_face_point<P, R, T0>(Xr, K, std::make_integer_sequence<int, RefPattern<P>::NFN>{});
-      if (valid) trF[(static_cast<size_t>(m * Dm::NQT + r) * 8 + v) * Z + z] = s * iJF[r];
-    } else {
-      constexpr int idx = r - Dm::NQT;
-      R s = vt_edge_point<P, R, T0>(Xr, K, std::make_integer_sequence<int, RefPattern<P>::NEN>{});
+  using L = VtLayout<P, R>;
+  using Dm = Dim<P>;
+  constexpr int m = T / IT::NE, e = T % IT::NE;
+  const R* row = XFz + (m * 8 + v) * L::NP;
+  if constexpr (e < 6) {
+    R Xs[RP::NFN];
+    vt_gather<P, R, e * RP::NFN>(row, Xs, std::make_integer_sequence<int, RP::NFN>{});
+    constexpr int f0 = IT::foff(e);
+#pragma unroll 1
+    for (int q = 0; q < IT::np(e); ++q) {
+      const R* ps = K.psiFc + (f0 + q) * RP::NFN;
+      R s = R(0);
+#pragma unroll
+      for (int a = 0; a < RP::NFN; ++a) s += ps[a] * Xs[a];
+      if (valid) trF[(static_cast<size_t>(m * Dm::NQT + f0 + q) * 8 + v) * Z + z] = s * iJF[f0 + q];
+    }
+  } else {
+    constexpr int le = e - 6;
+    R Xs[RP::NEN];
+    vt_gather<P, R, 6 * RP::NFN + le * RP::NEN>(row, Xs, std::make_integer_sequence<int, RP::NEN>{});
+#pragma unroll 1
+    for (int q = 0; q < Dm::NS; ++q) {
+      const int idx = le * Dm::NS + q;
+      const R* ps = K.psiEc + idx * RP::NEN;
+      R s = R(0);
+#pragma unroll
+      for (int a = 0; a < RP::NEN; ++a) s += ps[a] * Xs[a];
       if (valid) trE[(static_cast<size_t>(m * 12 * Dm::NS + idx) * 8 + v) * Z + z] = s * iJE[idx];
     }
-    vt_points<P, R, T0 + 1, T1>(Xr, v, K, iJF, iJE, trF, trE, Z, z, valid);
   }
 }
 
-// points [T0, T1) of group g, level by level (each level's values loaded once)
 template <int P, typename R, int T0, int T1>
-__device__ __forceinline__ void vt_point_levels(const R* XFz, int v, const RefConst<P, R>& K, const R* iJF,
-                                                const R* iJE, R* trF, R* trE, long long Z, long long z, bool valid) {
+__device__ __forceinline__ void vt_items(const R* XFz, int v, const RefConst<P, R>& K, const R* iJF, const R* iJE,
+                                         R* trF, R* trE, long long Z, long long z, bool valid) {
   if constexpr (T0 < T1) {
-    using PT = VtPoints<P>;
-    using L = VtLayout<P, R>;
-    constexpr int N = Dim<P>::N, CH = Chunk<R>::CH, m = T0 / PT::NPL;
-    constexpr int Tend = ((m + 1) * PT::NPL < T1) ? (m + 1) * PT::NPL : T1;
-    R Xr[((N + CH - 1) / CH) * CH];
-    const R* row = XFz + (m * 8 + v) * L::NP;
-#pragma unroll
-    for (int cc = 0; cc < (N + CH - 1) / CH; ++cc) ld16(row + cc * CH, Xr + cc * CH);
-    vt_points<P, R, T0, Tend>(Xr, v, K, iJF, iJE, trF, trE, Z, z, valid);
-    vt_point_levels<P, R, Tend, T1>(XFz, v, K, iJF, iJE, trF, trE, Z, z, valid);
+    vt_item<P, R, T0>(XFz, v, K, iJF, iJE, trF, trE, Z, z, valid);
+    vt_items<P, R, T0 + 1, T1>(XFz, v, K, iJF, iJE, trF, trE, Z, z, valid);
   }
 }
 
@@ -214,9 +221,9 @@ template <int P, typename R, int G = 0>
 __device__ __forceinline__ void vt_traces_group(int g, const R* XFz, int v, const RefConst<P, R>& K, const R* iJF,
                                                 const R* iJE, R* trF, R* trE, long long Z, long long z, bool valid) {
   if constexpr (G < RefPattern<P>::G) {
-    using PT = VtPoints<P>;
+    using IT = VtItems<P>;
     if (g == G)
-      vt_point_levels<P, R, PT::start(G), PT::start(G + 1)>(XFz, v, K, iJF, iJE, trF, trE, Z, z, valid);
+      vt_items<P, R, IT::start(G), IT::start(G + 1)>(XFz, v, K, iJF, iJE, trF, trE, Z, z, valid);
     else
       vt_traces_group<P, R, G + 1>(g, XFz, v, K, iJF, iJE, trF, trE, Z, z, valid);
   }
