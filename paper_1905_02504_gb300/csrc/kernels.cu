@@ -633,8 +633,10 @@ __device__ __forceinline__ void team_flux_difference(const R* Uh, R* dF, R iJ, c
 // the zone means, the KKT right-hand side of the divergence-free reconstruction
 // (zone B modes, nodal normal fields, face means; Sec. IV.b steps 5-8), then the
 // zone-mean B of step 10 (written back to U) and the time-step factor dt / q^k.
-// SM is any shared-memory struct with members in, W, Uz and fs per zone.
-template <int P, typename R, typename SM>
+// SM is any shared-memory struct with members in, W, Uz and fs per zone.  With
+// WRITE_U false (the reverse sweep, which reads a pristine checkpoint) the
+// zone-mean B is not written back.
+template <int P, typename R, typename SM, bool WRITE_U = true>
 __device__ __forceinline__ void team_load_inputs(SM& S, const DevTables& T, double* __restrict__ U,
                                                  const double* __restrict__ phi, const R* __restrict__ Wc,
                                                  const R* __restrict__ Bp, double dt, long long zbase, int tid) {
@@ -695,7 +697,7 @@ __device__ __forceinline__ void team_load_inputs(SM& S, const DevTables& T, doub
       R s = R(0);
       for (int b = 0; b < NBIN; ++b) s += GB[b * NR + d] * S.in[zl][b];
       S.Uz[zl][5 + d] = s;
-      U[(5 + d) * Z + z] = static_cast<double>(s);
+      if constexpr (WRITE_U) U[(5 + d) * Z + z] = static_cast<double>(s);
       if (d == 0) S.fs[zl] = static_cast<R>(dt / T.qpow[z % nr]);  // one FP64 division per zone
     }
   }
@@ -1394,6 +1396,7 @@ __global__ void k_fma_probe(T_* out, int iters, T_ a, T_ b) {
 inline unsigned grid_for(long long n) { return static_cast<unsigned>((n + TPB - 1) / TPB); }
 
 #include "adjoint_kernels.inc"
+#include "adjoint_team.inc"
 
 // objective of the differentiation workload: J = sum over the outer radial faces of
 // Phi_f^2 / A_f (the integral of <B_r>^2 over r_out); one block, deterministic
@@ -1460,6 +1463,11 @@ cudaError_t upload_reference_constants(const Tables& T) {
           if (!in_pat[al][T.Drow[al * Dm::NNZ + t]][j]) return cudaErrorInvalidValue;
     for (int t = 0; t < 6 * Dm::NFN; ++t)
       if (T.fnode[t] != RP::FN[t]) return cudaErrorInvalidValue;
+    // the node-team reverse predictor holds each column of D^alpha in AdjCols<P>::CL slots
+    for (int al = 0; al < 3; ++al)
+      for (int j = 0; j < Dm::N; ++j)
+        if (T.Dptr[al * (Dm::N + 1) + j + 1] - T.Dptr[al * (Dm::N + 1) + j] > AdjCols<P>::CL)
+          return cudaErrorInvalidValue;
     for (int t = 0; t < 12 * Dm::NEN; ++t)
       if (T.enode[t] != RP::EN[t]) return cudaErrorInvalidValue;
   }
@@ -1547,6 +1555,26 @@ GEO_INSTANTIATE(3, float)
 GEO_INSTANTIATE(4, float)
 #undef GEO_INSTANTIATE
 
+// the reverse predictor: the node team, or one thread per zone when the forward
+// predictor runs one thread per zone
+template <int P>
+cudaError_t launch_adj_ader(const DevTables& T, const DevState& S, const AdjState& A, double dt, cudaStream_t st) {
+  const double* Wc = static_cast<const double*>(S.Wc);
+  const double* Bp = static_cast<const double*>(S.Bp);
+  if (T.predictor == GEO_PRED_ZONE_THREAD) {
+    k_adj_ader<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.phi, Wc, Bp, A, dt);
+    return cudaGetLastError();
+  }
+  using L = AdjTeamLayout<P>;
+  constexpr int ZB = Team<P>::ZB;
+  cudaError_t e = cudaFuncSetAttribute(k_adj_ader_team<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(L::bytes));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
+  k_adj_ader_team<P><<<grid, ZB * Dim<P>::N, L::bytes, st>>>(T, S.phi, Wc, Bp, A, dt);
+  return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState& A, double dt, cudaStream_t st) {
   const double* Wc = static_cast<const double*>(S.Wc);
@@ -1556,7 +1584,8 @@ cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState
   k_adj_cot<<<grid_for(T.F + T.E), TPB, 0, st>>>(T, A);
   k_adj_face<P><<<grid_for(T.F), TPB, 0, st>>>(T, trF, A, dt);
   k_adj_edge<P><<<grid_for(T.E), TPB, 0, st>>>(T, trE, A, dt);
-  k_adj_ader<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.phi, Wc, Bp, A, dt);
+  cudaError_t e = launch_adj_ader<P>(T, S, A, dt, st);
+  if (e != cudaSuccess) return e;
   k_adj_bperp<P><<<grid_for(T.F), TPB, 0, st>>>(T, S.phi, Wc, A);
   k_adj_weno<P><<<grid_for(T.Z), TPB, 0, st>>>(T, A);
   return cudaGetLastError();
@@ -1568,7 +1597,7 @@ cudaError_t launch_adjoint_stage(int stage, const DevTables& T, const DevState& 
   const double* Bp = static_cast<const double*>(S.Bp);
   switch (stage) {
     case ST_WENO: k_adj_weno<P><<<grid_for(T.Z), TPB, 0, st>>>(T, A); break;
-    case ST_ADER: k_adj_ader<P><<<grid_for(T.Z), TPB, 0, st>>>(T, S.phi, Wc, Bp, A, dt); break;
+    case ST_ADER: return launch_adj_ader<P>(T, S, A, dt, st);
     case ST_FACE: k_adj_face<P><<<grid_for(T.F), TPB, 0, st>>>(T, static_cast<const double*>(S.trF), A, dt); break;
     case ST_EDGE: k_adj_edge<P><<<grid_for(T.E), TPB, 0, st>>>(T, static_cast<const double*>(S.trE), A, dt); break;
     default: return cudaErrorInvalidValue;

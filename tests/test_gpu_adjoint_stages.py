@@ -104,3 +104,25 @@ def test_stage_transpose(n, nr, p, stage):
         checked += 1
     assert checked >= 2, checked
     mesh.close()
+
+
+@pytest.mark.parametrize("n,nr,p", [(4, 3, 2), (4, 3, 3), (3, 5, 4)])
+def test_reverse_predictor_schedules_agree(n, nr, p):
+    """The node-team reverse predictor (default) and the one-thread-per-zone one
+    (used with GEO_PRED_ZONE_THREAD) apply the same transpose: their cotangents
+    of the Taylor coefficients agree to rounding."""
+    from paper_1905_02504_gb300 import geomhd
+    g = geomhd
+    o, mesh, U0, phi = setup_case(n, nr, p)
+    rng = np.random.default_rng(11 + p)
+    U = np.ascontiguousarray((U0 * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, U0.shape))).T)
+    dt = o.cfl_dt(U.T, 0.4)
+    M, nqt, ns, nc1 = p, sum(o.dfb.nq), {2: 1, 3: 2, 4: 3}[p], len(o.weno.exps)
+    n_out = (M - 1) * nqt * 8 * mesh.Z + (M - 1) * 12 * ns * 8 * mesh.Z
+    w = rng.standard_normal(n_out)
+    out = []
+    for sched in (geomhd.GEO_PRED_NODE_TEAM, geomhd.GEO_PRED_ZONE_THREAD):
+        g.geo_set_predictor(mesh.h, sched)
+        out.append(g.geo_debug_stage_vjp(mesh.h, ST_ADER, dt, U, phi, w, 8 * nc1 * mesh.Z))
+    assert np.abs(out[0] - out[1]).max() <= 1e-12 * np.abs(out[1]).max()
+    mesh.close()
