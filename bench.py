@@ -92,13 +92,19 @@ def workload_name(a):
         6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order, form, getattr(a, "problem", "smooth"), extra)
 
 
-def kernel_name(stage, pred, positivity=False):
+def default_schedule(order):
+    """The library's default predictor schedule: the variable-layout team at
+    orders 2 and 3, the node team at order 4."""
+    return 2 if order <= 3 else 1
+
+
+def kernel_name(stage, pred, positivity=False, order=4):
     """Name of the kernel that runs a stage (the predictor stage has three
     schedules; the variable-layout one runs the node team when positivity is on)."""
     name = "k_" + stage
     if stage == "ader":
         if pred is None:
-            pred = 1
+            pred = default_schedule(order)
         if pred == 2 and not positivity:
             name += "_vt"
         elif pred != 0:
@@ -106,10 +112,10 @@ def kernel_name(stage, pred, positivity=False):
     return name
 
 
-def sched_name(pred, fp32):
-    """Predictor schedule in use (the library default is the node team)."""
+def sched_name(pred, order):
+    """Predictor schedule in use."""
     if pred is None:
-        pred = 1
+        pred = default_schedule(order)
     return {0: "zone-thread", 1: "node-team", 2: "variable-team"}[pred]
 
 
@@ -377,16 +383,16 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "ms_per_step": t_ms / a.steps, "dtype": "f32 bulk / f64 accumulation and updates",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": achieved / nominal_fp32,
-                     "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), m32.Z,
+                     "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order), m32.Z,
                                                 "fp32"),
-                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity),
+                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order),
                      "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
                                   "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
                      "measured_fp32_fma_tflops": fp32_probe},
         "stages": {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
                    for s in range(geomhd.N_STAGES)},
         "rel_l1_vs_fp64": err, "rel_l1_phi_vs_fp64": errp, "steps_compared": a.compare_steps,
-        "predictor": sched_name(a.predictor, True),
+        "predictor": sched_name(a.predictor, a.order),
         "divB_rel": r32,
     }
     m32.close()
@@ -529,9 +535,9 @@ def gpu_arm(a):
         kind = "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak
     roofline = {"bound": "alu", "achieved": achieved, "peak": nominal, "unit": "TFLOP/s",
                 "frac": achieved / nominal,
-                "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), Z,
+                "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order), Z,
                                             "fp32" if a.fp32_only else "fp64"),
-                "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity), "peak_kind": kind, "measured_fma_tflops": fma_peak}
+                "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order), "peak_kind": kind, "measured_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
     fp32 = None if (a.no_fp32 or a.fp32_only) else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
@@ -545,7 +551,7 @@ def gpu_arm(a):
             "data": "synthetic",
             "config": {"workload": workload_name(a), "zones": Z, "order": a.order, "dt": dt,
                        "problem": a.problem, "positivity": a.positivity,
-                       "predictor": sched_name(a.predictor, a.fp32_only),
+                       "predictor": sched_name(a.predictor, a.order),
                        "cfl": a.cfl, "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             # per step: the seven stage kernels, the trace positivity kernel when the

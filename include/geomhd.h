@@ -113,14 +113,16 @@ int geo_set_riemann(geo_mesh_t mesh, int solver);
  * 8-10 and Eqs. C.34-C.36); all compute the same arithmetic:
  *   GEO_PRED_ZONE_THREAD (0): one thread per zone, its nodal states in
  *     thread-local memory;
- *   GEO_PRED_NODE_TEAM (1, default): one thread per serendipity node, a team of
- *     N threads per zone exchanging nodal fluxes through shared memory;
- *   GEO_PRED_VAR_TEAM (2): the node team, with the derivative contraction and
+ *   GEO_PRED_NODE_TEAM (1, default at order 4): one thread per serendipity node,
+ *     a team of N threads per zone exchanging nodal fluxes through shared memory;
+ *   GEO_PRED_VAR_TEAM (2, default at orders 2, 3): the node team, with the derivative contraction and
  *     the face / edge point evaluations done by one thread per (zone, variable,
  *     row group) on the compiled nonzero pattern of D^alpha; with positivity on
  *     the node-team kernel runs instead.
- * They differ only in the summation order of the flux-difference rows.
- * Returns GEO_ERR_ARG for any other value. */
+ * They differ only in the summation order of the flux-difference rows.  The
+ * reverse sweep of geo_step_adjoint runs its predictor as a node team, or one
+ * thread per zone with GEO_PRED_ZONE_THREAD.  Returns GEO_ERR_ARG for any other
+ * value. */
 enum { GEO_PRED_ZONE_THREAD = 0, GEO_PRED_NODE_TEAM = 1, GEO_PRED_VAR_TEAM = 2 };
 int geo_set_predictor(geo_mesh_t mesh, int schedule);
 

