@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--predictor", type=int, default=None, choices=[0, 1, 2],
                     help="predictor schedule: 0 one thread per zone, 1 one thread per node, 2 the node team "
                          "with the contraction in the variable layout (default: the library's)")
+    ap.add_argument("--contraction", action="store_true",
+                    help="time the predictor's derivative contraction alone (FP32, CUDA-core and tensor-core "
+                         "forms) beside the FP32-bulk predictor kernel on the same workload")
     ap.add_argument("--sample-n", type=int, default=4)
     ap.add_argument("--sample-nr", type=int, default=4)
     return ap.parse_args()
@@ -92,19 +95,19 @@ def workload_name(a):
         6, a.n, a.n, a.nr, 6 * a.n * a.n * a.nr, a.order, form, getattr(a, "problem", "smooth"), extra)
 
 
-def default_schedule(order):
+def default_schedule(order, fp32=False):
     """The library's default predictor schedule: the variable-layout team at
-    orders 2 and 3, the node team at order 4."""
-    return 2 if order <= 3 else 1
+    orders 2 and 3 and for the FP32-bulk form, the node team for FP64 at order 4."""
+    return 2 if (order <= 3 or fp32) else 1
 
 
-def kernel_name(stage, pred, positivity=False, order=4):
+def kernel_name(stage, pred, positivity=False, order=4, fp32=False):
     """Name of the kernel that runs a stage (the predictor stage has three
     schedules; the variable-layout one runs the node team when positivity is on)."""
     name = "k_" + stage
     if stage == "ader":
         if pred is None:
-            pred = default_schedule(order)
+            pred = default_schedule(order, fp32)
         if pred == 2 and not positivity:
             name += "_vt"
         elif pred != 0:
@@ -112,10 +115,10 @@ def kernel_name(stage, pred, positivity=False, order=4):
     return name
 
 
-def sched_name(pred, order):
+def sched_name(pred, order, fp32=False):
     """Predictor schedule in use."""
     if pred is None:
-        pred = default_schedule(order)
+        pred = default_schedule(order, fp32)
     return {0: "zone-thread", 1: "node-team", 2: "variable-team"}[pred]
 
 
@@ -295,8 +298,10 @@ PREDICTOR_SOURCES = ("device.cuh", "mhd_device.cuh", "ader_vt.cuh")
 
 def predictor_fingerprint():
     """sha256 prefix of the predictor kernels' source: the node-team section of
-    kernels.cu (from the team sizes to the face-flux stage), ader_vt.cuh and the
-    device headers they use.  Edits elsewhere in the library leave it unchanged."""
+    kernels.cu (from the team sizes to the face-flux stage), ader_vt.cuh, the
+    device headers they use and the generator of the compiled pattern
+    (refpattern.py, whose row groups set the variable team's work split).
+    Edits elsewhere in the library leave it unchanged."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1905_02504_gb300", "csrc")
     k = open(os.path.join(csrc, "kernels.cu")).read()
@@ -305,6 +310,7 @@ def predictor_fingerprint():
     h = hashlib.sha256(k[a:b].encode())
     for f in PREDICTOR_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_1905_02504_gb300", "refpattern.py"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -383,16 +389,16 @@ def fp32_bulk_leg(a, mesh64, U0, phi0, dt, stream, flush, barrier, ws):
         "ms_per_step": t_ms / a.steps, "dtype": "f32 bulk / f64 accumulation and updates",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_fp32, "unit": "TFLOP/s",
                      "frac": achieved / nominal_fp32,
-                     "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order), m32.Z,
+                     "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order, True), m32.Z,
                                                 "fp32"),
-                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order),
+                     "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order, True),
                      "peak_kind": "nominal GB300 FP32 (152 SMs x 128 FMA/clk x 2.07 GHz); measured FP32 "
                                   "FMA-chain probe %.1f TFLOP/s" % fp32_probe,
                      "measured_fp32_fma_tflops": fp32_probe},
         "stages": {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
                    for s in range(geomhd.N_STAGES)},
         "rel_l1_vs_fp64": err, "rel_l1_phi_vs_fp64": errp, "steps_compared": a.compare_steps,
-        "predictor": sched_name(a.predictor, a.order),
+        "predictor": sched_name(a.predictor, a.order, True),
         "divB_rel": r32,
     }
     m32.close()
@@ -535,9 +541,11 @@ def gpu_arm(a):
         kind = "nominal GB300 FP64 (recipe); measured FP64 FMA-chain probe %.3f TFLOP/s" % fma_peak
     roofline = {"bound": "alu", "achieved": achieved, "peak": nominal, "unit": "TFLOP/s",
                 "frac": achieved / nominal,
-                "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order), Z,
+                "traffic": captured_traffic(a, kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order,
+                                                           a.fp32_only), Z,
                                             "fp32" if a.fp32_only else "fp64"),
-                "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order), "peak_kind": kind, "measured_fma_tflops": fma_peak}
+                "kernel": kernel_name(geomhd.STAGES[top], a.predictor, a.positivity, a.order, a.fp32_only),
+                "peak_kind": kind, "measured_fma_tflops": fma_peak}
     stages = {geomhd.STAGES[s]: {"avg_ms": float(avg[s]), "share": float(stage_ms[s] / stage_ms.sum())}
               for s in range(geomhd.N_STAGES)}
     fp32 = None if (a.no_fp32 or a.fp32_only) else fp32_bulk_leg(a, mesh, U0, phi0, dt, stream, flush, barrier, ws)
@@ -551,7 +559,7 @@ def gpu_arm(a):
             "data": "synthetic",
             "config": {"workload": workload_name(a), "zones": Z, "order": a.order, "dt": dt,
                        "problem": a.problem, "positivity": a.positivity,
-                       "predictor": sched_name(a.predictor, a.order),
+                       "predictor": sched_name(a.predictor, a.order, a.fp32_only),
                        "cfl": a.cfl, "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             # per step: the seven stage kernels, the trace positivity kernel when the
@@ -598,12 +606,16 @@ def adjoint_arm(a):
     torch.cuda.set_device(local)
     prec = geomhd.GEO_FP32_BULK if a.fp32_only else geomhd.GEO_FP64
     mesh = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order, prec=prec)
+    if a.predictor is not None:
+        geomhd.geo_set_predictor(mesh.h, a.predictor)
     U0, phi0 = mesh.initial_state(make_problem(a.problem, noise=a.noise), nq_zone=a.nq_zone or None,
                                   nq_edge=a.nq_edge)
     mesh.upload(U0, phi0)
     dt = mesh.cfl_dt(a.cfl)
     Z, F, E = mesh.Z, mesh.F, mesh.E
     ref64 = geomhd.Mesh(a.n, a.nr, 1.0, 2.0, a.order) if a.fp32_only else None
+    if ref64 is not None and a.predictor is not None:
+        geomhd.geo_set_predictor(ref64.h, a.predictor)
     Ut0 = torch.from_numpy(np.ascontiguousarray(U0)).cuda()
     pt0 = torch.from_numpy(phi0.copy()).cuda()
     rng = np.random.default_rng(1905)
@@ -742,10 +754,66 @@ def convergence_arm(a):
               flush=True)
 
 
+def contraction_arm(a):
+    """The predictor's contraction sum_alpha D^alpha F^alpha (Eq. C.34) timed alone,
+    as many times per zone as the FP32-bulk predictor performs it (level 1, then
+    p Picard iterations over levels 2..M), in the CUDA-core form of the variable
+    team and in a tensor-core form (mma.sync TF32, three passes), beside the
+    predictor kernel's own time per step on the same mesh."""
+    import numpy as np
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    from paper_1905_02504_gb300.inputs import domain, make_problem
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    p = a.order
+    a.fp32_only = True
+    mesh = geomhd.Mesh(a.n, a.nr, *domain(a.problem), p, prec=geomhd.GEO_FP32_BULK, stream=stream.cuda_stream,
+                       gamma=make_problem(a.problem).gamma)
+    pred = default_schedule(p, True) if a.predictor is None else a.predictor
+    geomhd.geo_set_predictor(mesh.h, pred)
+    U0, phi0 = mesh.initial_state(make_problem(a.problem))
+    mesh.upload(U0, phi0)
+    dt = mesh.cfl_dt(a.cfl)
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            mesh.step(dt)
+    torch.cuda.synchronize()
+    geomhd.geo_set_stage_timing(mesh.h, 1)
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            mesh.step(dt)
+    torch.cuda.synchronize()
+    geomhd.geo_set_stage_timing(mesh.h, 0)
+    stage_ms, stage_cnt = geomhd.geo_get_stage_timing(mesh.h)
+    pred_ms = stage_ms[2] / max(int(stage_cnt[2]), 1)
+    Z = mesh.Z
+    N = {2: 8, 3: 20, 4: 32}[p]
+    nnz = {2: 16, 3: 96, 4: 192}[p]
+    reps = 1 + p * (p - 1)
+    out = torch.empty((Z, 8, N), dtype=torch.float32, device="cuda")
+    forms = {}
+    for tensor, name in ((0, "cuda_core_sparse"), (1, "mma_sync_tf32x3_dense")):
+        ms = [geomhd.geo_probe_contraction(mesh.h, tensor, Z, reps, out) for _ in range(3)]
+        t = float(np.median(ms))
+        useful = 2.0 * 3 * nnz * 8 * reps * Z
+        forms[name] = {"ms": round(t, 4), "share_of_predictor": round(t / pred_ms, 3),
+                       "useful_tflops": round(useful / (t * 1e-3) / 1e12, 2)}
+    mp, kp = (N + 15) // 16 * 16, (3 * N + 7) // 8 * 8
+    forms["mma_sync_tf32x3_dense"]["issued_tflops"] = round(
+        3 * 2.0 * mp * kp * 8 * reps * Z / (forms["mma_sync_tf32x3_dense"]["ms"] * 1e-3) / 1e12, 1)
+    print(json.dumps({"study": "predictor contraction alone, FP32", "workload": workload_name(a), "order": p,
+                      "zones": Z, "contractions_per_zone": reps, "predictor_schedule": sched_name(pred, p, True),
+                      "predictor_ms_per_step": round(pred_ms, 4), "forms": forms}), flush=True)
+    mesh.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+    elif a.contraction:
+        contraction_arm(a)
     elif a.convergence:
         convergence_arm(a)
     elif a.adjoint:

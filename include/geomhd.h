@@ -113,9 +113,11 @@ int geo_set_riemann(geo_mesh_t mesh, int solver);
  * 8-10 and Eqs. C.34-C.36); all compute the same arithmetic:
  *   GEO_PRED_ZONE_THREAD (0): one thread per zone, its nodal states in
  *     thread-local memory;
- *   GEO_PRED_NODE_TEAM (1, default at order 4): one thread per serendipity node,
- *     a team of N threads per zone exchanging nodal fluxes through shared memory;
- *   GEO_PRED_VAR_TEAM (2, default at orders 2, 3): the node team, with the derivative contraction and
+ *   GEO_PRED_NODE_TEAM (1, default for GEO_FP64 at order 4): one thread per
+ *     serendipity node, a team of N threads per zone exchanging nodal fluxes
+ *     through shared memory;
+ *   GEO_PRED_VAR_TEAM (2, default at orders 2, 3 and for GEO_FP32_BULK at order
+ *     4): the node team, with the derivative contraction and
  *     the face / edge point evaluations done by one thread per (zone, variable,
  *     row group) on the compiled nonzero pattern of D^alpha; with positivity on
  *     the node-team kernel runs instead.
@@ -233,6 +235,19 @@ int geo_stage_flops(geo_mesh_t mesh, double* flops_per_unit, int64_t* units);
 /* Measured FMA throughput of this GPU for the precision: a dependent-chain
  * microbenchmark; result in floating-point operations per second (synchronises). */
 int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s);
+
+/* Measurement probe of the predictor's derivative contraction (Eq. C.34,
+ * dF_{v,i} = sum_alpha sum_j D^alpha_ij F^alpha_{v,j}) alone, FP32, on the mesh's
+ * order: tensor = 0 times the CUDA-core sparse form of the variable-team
+ * predictor, tensor = 1 a tensor-core form (mma.sync TF32, three-pass split,
+ * dense padded D).  F of each zone is a fixed hash of (zone, alpha, v, j) made on
+ * the device (no HBM reads); the contraction runs `reps` times per zone over
+ * `zones` zones and the last result goes to out_dev (device, zones x 8 x N
+ * floats, [zone][v][node], caller-owned).  *ms = duration of one launch (CUDA
+ * events on the mesh's stream, after one untimed launch; synchronises).  Needs a
+ * GEO_FP32_BULK mesh (its FP32 reference constants); GEO_ERR_ARG otherwise, or if
+ * zones exceeds 2^28.  Not part of geo_step. */
+int geo_probe_contraction(geo_mesh_t mesh, int tensor, int64_t zones, int reps, float* out_dev, float* ms);
 
 /* Copy one internal work buffer of the last step to host memory, for stage-by-
  * stage verification: which = 0 WENO-AO Taylor coefficients [8][NC1][Z],

@@ -8,6 +8,7 @@
 
 #include "../../include/geomhd.h"
 #include "device.cuh"
+#include "probe.h"
 #include "host_tables.h"
 
 namespace {
@@ -172,8 +173,9 @@ int geo_mesh_create(int subdiv, int nr, double r_in, double r_out, int order, in
   D.gamma = 5.0 / 3.0;
   D.positivity = 0;
   // default schedule: the variable-layout team where it measured faster (orders
-  // 2, 3), the node team at order 4 (equal in FP32, 2 % faster in FP64)
-  D.predictor = order <= 3 ? GEO_PRED_VAR_TEAM : GEO_PRED_NODE_TEAM;
+  // 2, 3, and the FP32-bulk form at order 4), the node team for FP64 at order 4
+  // (3 % faster there)
+  D.predictor = (order <= 3 || prec == GEO_FP32_BULK) ? GEO_PRED_VAR_TEAM : GEO_PRED_NODE_TEAM;
   D.riemann = GEO_RIEMANN_HLL;
   std::vector<double> qpow(T.nr + 2);
   for (int k = 0; k < T.nr + 2; ++k) qpow[k] = std::pow(T.q, k);
@@ -781,6 +783,16 @@ int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s) {
   if (!flops_per_s) return fail(GEO_ERR_ARG, "bad arguments");
   cudaError_t e = geo::probe_fma(prec, static_cast<cudaStream_t>(stream), flops_per_s);
   if (e != cudaSuccess) return cuda_fail(e, "fma probe");
+  return GEO_OK;
+}
+
+int geo_probe_contraction(geo_mesh_t m, int tensor, int64_t zones, int reps, float* out_dev, float* ms) {
+  if (!m || !out_dev || !ms || zones < 1 || reps < 1 || (tensor != 0 && tensor != 1))
+    return fail(GEO_ERR_ARG, "geo_probe_contraction: bad arguments");
+  if (m->prec != GEO_FP32_BULK) return fail(GEO_ERR_ARG, "geo_probe_contraction: needs a GEO_FP32_BULK mesh");
+  if (zones > (int64_t(1) << 31) / 8) return fail(GEO_ERR_ARG, "geo_probe_contraction: too many zones");
+  cudaError_t e = geo::probe_contraction_any(m->order, tensor, zones, reps, m->st, out_dev, ms);
+  if (e != cudaSuccess) return cuda_fail(e, "geo_probe_contraction");
   return GEO_OK;
 }
 

@@ -11,6 +11,7 @@
 // the time-integrated face fluxes and edge EMFs are accumulated in FP64 and the
 // updates of U and Phi are FP64 in both forms, so div B stays at FP64 rounding.
 #include "device.cuh"
+#include "probe.h"
 #include "geomhd.h"
 #include "host_tables.h"
 #include "mhd_device.cuh"
@@ -18,6 +19,7 @@
 
 #include <cfloat>
 #include <utility>
+#include <vector>
 
 namespace geo {
 
@@ -1681,5 +1683,7 @@ cudaError_t probe_fma(int prec, cudaStream_t st, double* flops_per_s) {
   *flops_per_s = flops / (ms * 1e-3);
   return cudaGetLastError();
 }
+
+#include "probe_contract.inc"
 
 }  // namespace geo

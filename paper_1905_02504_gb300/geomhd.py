@@ -60,6 +60,7 @@ _SIGS = {
     "geo_get_stage_timing": [_h, _vp, _vp],
     "geo_stage_flops": [_h, _vp, _vp],
     "geo_probe_fma_peak": [ctypes.c_int, _vp, _pd],
+    "geo_probe_contraction": [_h, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_float)],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_set_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_run_stage": [_h, ctypes.c_int, _d],
@@ -250,6 +251,14 @@ def geo_probe_fma_peak(prec=GEO_FP64, stream=0):
     v = _d()
     _check(_lib.geo_probe_fma_peak(prec, _vp(stream), ctypes.byref(v)), "geo_probe_fma_peak")
     return v.value
+
+
+def geo_probe_contraction(h, tensor, zones, reps, out):
+    """out: float32 CUDA tensor of zones x 8 x N elements; returns the launch's ms."""
+    ms = ctypes.c_float()
+    _check(_lib.geo_probe_contraction(h, int(tensor), int(zones), int(reps), _vp(out.data_ptr()), ctypes.byref(ms)),
+           "geo_probe_contraction")
+    return ms.value
 
 
 def geo_debug_buffer(h, which, count):

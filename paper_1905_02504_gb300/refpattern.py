@@ -123,7 +123,14 @@ def edge_nodes(p):
     return out
 
 
-ROW_GROUPS = {2: 1, 3: 2, 4: 4}
+# Row groups per (zone, variable) of the variable team: a thread computes the rows
+# of its group, so fewer groups reuse each loaded 16-byte chunk of F for more
+# rows (FP32 FMAs per chunk: about 8 with 4 groups at p = 4, 15 with 2; the
+# GB300 SM issues 128 FP32 FMAs per 128 B of shared-memory bandwidth, i.e. 16 per
+# chunk) but leave fewer threads for the phase.  Measured (FP32-bulk predictor):
+# p = 4, 4 -> 2 groups 27.6 -> 26.1 ms on 1,572,864 zones, 1 group 31.3 ms;
+# p = 3, 2 -> 1 group 0.85 -> 0.96 ms on 196,608 zones.
+ROW_GROUPS = {2: 1, 3: 2, 4: 2}
 
 
 def row_groups(p, pat):

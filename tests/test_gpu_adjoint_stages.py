@@ -13,10 +13,14 @@ stage's reverse kernel alone.
 
 The base state carries 10 % seeded noise (as in the full-step checks), so most
 MinMod / HLL / Rusanov and |beta_H - beta_k| decisions sit far from their
-switches compared with the +-2h stencil.  The differences are taken at three
-steps; where they do not settle at the fourth-order rate a switch was crossed and
-the direction is skipped (at least two of four must count); otherwise the
-adjoint must match their Richardson extrapolation."""
+switches compared with the +-2h stencil.  The face and edge directions touch a
+seeded 5 % of the point states, so that a stencil meets few of the solver
+decisions.  The differences are taken at three steps.  A direction counts when
+the two largest steps already agree to 2e-8 (truncation below rounding: the
+smooth predictor) or when the differences settle at the fourth-order rate;
+otherwise a switch was crossed and it is skipped (at least two of six must
+count).  The adjoint must match the Richardson extrapolation of the settled
+pair."""
 import numpy as np
 import pytest
 
@@ -86,9 +90,11 @@ def test_stage_transpose(n, nr, p, stage):
     x0 = base[stage]
     y0 = forward_stage(mesh, stage, dt, U, phi, x0, fixed)
     checked, seen = 0, []
-    for trial in range(4):
+    for trial in range(6):
         w = rng.standard_normal(y0.size)
         d = rng.uniform(-1.0, 1.0, x0.size) * np.maximum(np.abs(x0), 1e-3 * np.abs(x0).max())
+        if stage in (ST_FACE, ST_EDGE):
+            d *= rng.uniform(size=x0.size) < 0.05
 
         def fd(h):
             # difference the stage outputs first, then project: a projection of
@@ -98,11 +104,15 @@ def test_stage_transpose(n, nr, p, stage):
 
         f0, f1, f2 = (fd(h) for h in H)
         seen.append((f0, f1, f2))
-        # smooth within the stencils: the O(h^4) error shrinks ~256-fold per step
-        # (or is already at rounding); a switch crossed gives no such rate
-        if abs(f1 - f2) > max(abs(f0 - f1) / 16.0, 1e-9 * abs(f2)):
+        if abs(f0 - f1) <= 2e-8 * abs(f1):
+            # truncation already below rounding at the two largest steps
+            best = f1 + (f1 - f0) / 255.0
+        elif abs(f1 - f2) <= min(abs(f0 - f1) / 16.0, 1e-6 * abs(f2)):
+            # smooth within the stencils: the O(h^4) error shrinks ~256-fold per
+            # step; a switch crossed gives no such rate
+            best = f2 + (f2 - f1) / 255.0
+        else:
             continue
-        best = f2 + (f2 - f1) / 255.0
         gx = g.geo_debug_stage_vjp(mesh.h, stage, dt, U, phi, w, x0.size)
         adj = float(gx @ d)
         assert abs(adj - best) <= TOL * abs(best), (trial, adj, f0, f1, f2)
