@@ -48,6 +48,7 @@ struct geo_mesh {
   geo::DevState adj_fwd{};
   geo::AdjState adj{};
   double* adj_U0 = nullptr;
+  double* adj_It = nullptr;  // stored Picard iterates of the node-team reverse sweep
   double ms[geo::N_STAGES] = {};
   int64_t cnt[geo::N_STAGES] = {};
   // physical-state flag of the last step, copied to pinned host memory after
@@ -610,6 +611,8 @@ static int ensure_adjoint_buffers(geo_mesh* m) {
   A.gBpz = m->alloc(static_cast<size_t>(d.NQT) * Z, err);
   A.gphiz = m->alloc(6 * Z, err);
   A.U0 = m->adj_U0;
+  // [P-1][M-1][8][N][Z]: the linearisation points of the reverse predictor
+  m->adj_It = m->alloc(static_cast<size_t>(d.P - 1) * (d.M - 1) * 8 * d.N * Z, err);
   if (err != cudaSuccess) return cuda_fail(err, "adjoint buffers");
   m->adj_ready = true;
   return GEO_OK;
@@ -631,8 +634,19 @@ int geo_step_adjoint(geo_mesh_t m, double dt, const double* U_in, const double* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_fwd.U, U_in, 8 * Z * sizeof(double), cudaMemcpyDeviceToDevice, m->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->adj_fwd.phi, phi_in, F * sizeof(double), cudaMemcpyDeviceToDevice, m->st);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint checkpoint copy");
-  // forward intermediates of the checkpoint state
+  // forward intermediates of the checkpoint state; with a team schedule the
+  // predictor is the node team that also stores its Picard iterates, which the
+  // reverse predictor then reads instead of recomputing them
+  const bool store = m->dt.predictor != GEO_PRED_ZONE_THREAD;
   for (int s = geo::ST_WENO; s <= geo::ST_ADER && e == cudaSuccess; ++s) {
+    if (s == geo::ST_ADER && store) {
+      switch (m->order) {
+        case 2: e = geo::launch_ader_store_iterates<2>(m->dt, m->adj_fwd, m->adj_It, dt, m->st); break;
+        case 3: e = geo::launch_ader_store_iterates<3>(m->dt, m->adj_fwd, m->adj_It, dt, m->st); break;
+        default: e = geo::launch_ader_store_iterates<4>(m->dt, m->adj_fwd, m->adj_It, dt, m->st); break;
+      }
+      continue;
+    }
     switch (m->order) {
       case 2: e = geo::launch_stage<2, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
       case 3: e = geo::launch_stage<3, double>(s, m->dt, m->adj_fwd, dt, m->st); break;
@@ -641,6 +655,7 @@ int geo_step_adjoint(geo_mesh_t m, double dt, const double* U_in, const double* 
   }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint forward recompute");
   geo::AdjState A = m->adj;
+  A.It = store ? m->adj_It : nullptr;
   A.gUp = gU_out;
   A.gphip = gphi_out;
   A.gU = gU_in;

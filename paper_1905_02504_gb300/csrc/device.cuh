@@ -108,6 +108,9 @@ struct AdjState {
   double* gBpz;         // [NQT][Z] cotangent of the zone's KKT inputs from the face fields
   double* gphiz;        // [6][Z]   cotangent of the zone's face-mean inputs
   const double* U0;     // [8][Z] checkpoint state (read only, pristine)
+  // Picard iterates of the checkpoint's predictor stored by its forward recompute
+  // ([P-1][M-1][8][N][Z]), or null: the reverse predictor then recomputes them
+  const double* It = nullptr;
 };
 
 enum Stage { ST_WENO = 0, ST_BPERP, ST_ADER, ST_FACE, ST_EDGE, ST_UPD_U, ST_UPD_PHI, N_STAGES };
@@ -120,6 +123,10 @@ cudaError_t upload_reference_constants(const Tables& T);
 // launchers (kernels.cu); return cudaGetLastError() of the launch
 template <int P, typename R>
 cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, double dt, cudaStream_t st);
+// the FP64 node-team predictor (no positivity) that also stores its Picard
+// iterates for the reverse sweep (It: [P-1][M-1][8][N][Z] doubles)
+template <int P>
+cudaError_t launch_ader_store_iterates(const DevTables& T, const DevState& S, double* It, double dt, cudaStream_t st);
 cudaError_t launch_cfl(const DevTables& T, const DevState& S, double cfl, double* out_host,
                        cudaStream_t st);
 cudaError_t launch_divb(const DevTables& T, const DevState& S, double* out2_host, cudaStream_t st);

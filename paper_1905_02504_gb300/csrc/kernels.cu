@@ -767,11 +767,13 @@ template <> struct TeamOcc<2, double> { static constexpr int MINB = 4; };
 template <> struct TeamOcc<3, double> { static constexpr int MINB = 2; };
 template <> struct TeamOcc<4, double> { static constexpr int MINB = 2; };
 
-template <int P, typename R, bool POS>
+// STORE: also write the levels after each of the first P-1 Picard iterations to
+// itS ([P-1][M-1][8][N][Z]), the linearisation points of the reverse sweep
+template <int P, typename R, bool POS, bool STORE = false>
 __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
     k_ader_team(const DevTables T, double* __restrict__ U, const double* __restrict__ phi,
                 const R* __restrict__ Wc, const R* __restrict__ Bp, R* __restrict__ trF, R* __restrict__ trE,
-                double dt) {
+                double dt, R* __restrict__ itS) {
   using Dm = Dim<P>;
   constexpr int N = Dm::N, M = Dm::M, NC1 = Dm::NC1, NC = Dm::NC, NQT = Dm::NQT, NS = Dm::NS,
                 NBIN = Dm::NBIN, NR = 3 + 3 * Dm::N, ZB = Team<P>::ZB, NT = ZB * N;
@@ -868,6 +870,12 @@ __global__ void __launch_bounds__(Team<P>::ZB * Dim<P>::N, TeamOcc<P, R>::MINB)
 #pragma unroll
         for (int m = 1; m < M; ++m) s -= rk[m] * dF[m][v];
         Uh[kk][v] = s;
+      }
+      if constexpr (STORE) {
+        if (it < P - 1 && valid) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) itS[((static_cast<size_t>(it * (M - 1) + kk - 1) * 8 + v) * N + i) * Z + z] = Uh[kk][v];
+        }
       }
     }
   }
@@ -1515,9 +1523,9 @@ cudaError_t launch_stage(int stage, const DevTables& T, const DevState& S, doubl
         constexpr int ZB = Team<P>::ZB;
         const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
         if (T.positivity)
-          k_ader_team<P, R, true><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+          k_ader_team<P, R, true><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt, nullptr);
         else
-          k_ader_team<P, R, false><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
+          k_ader_team<P, R, false><<<grid, ZB * Dim<P>::N, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt, nullptr);
       } else if (T.positivity) {
         k_ader<P, R, true><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, S.phi, Wc, Bp, trF, trE, dt);
         k_pos_traces<P, R><<<grid_for(T.Z), TPB, 0, st>>>(T, S.U, trF, trE);
@@ -1569,13 +1577,30 @@ cudaError_t launch_adj_ader(const DevTables& T, const DevState& S, const AdjStat
   }
   using L = AdjTeamLayout<P>;
   constexpr int ZB = Team<P>::ZB;
-  cudaError_t e = cudaFuncSetAttribute(k_adj_ader_team<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(L::bytes));
-  if (e != cudaSuccess) return e;
   const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
-  k_adj_ader_team<P><<<grid, ZB * Dim<P>::N, L::bytes, st>>>(T, S.phi, Wc, Bp, A, dt);
+  // with the iterates stored by the forward recompute, the team skips its own
+  // forward Picard sweep
+  auto run = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::bytes));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, ZB * Dim<P>::N, L::bytes, st>>>(T, S.phi, Wc, Bp, A, dt);
+    return cudaGetLastError();
+  };
+  return A.It ? run(k_adj_ader_team<P, true>) : run(k_adj_ader_team<P, false>);
+}
+
+template <int P>
+cudaError_t launch_ader_store_iterates(const DevTables& T, const DevState& S, double* It, double dt, cudaStream_t st) {
+  constexpr int ZB = Team<P>::ZB;
+  const unsigned grid = static_cast<unsigned>((T.Z + ZB - 1) / ZB);
+  k_ader_team<P, double, false, true><<<grid, ZB * Dim<P>::N, 0, st>>>(
+      T, S.U, S.phi, static_cast<const double*>(S.Wc), static_cast<const double*>(S.Bp), static_cast<double*>(S.trF),
+      static_cast<double*>(S.trE), dt, It);
   return cudaGetLastError();
 }
+template cudaError_t launch_ader_store_iterates<2>(const DevTables&, const DevState&, double*, double, cudaStream_t);
+template cudaError_t launch_ader_store_iterates<3>(const DevTables&, const DevState&, double*, double, cudaStream_t);
+template cudaError_t launch_ader_store_iterates<4>(const DevTables&, const DevState&, double*, double, cudaStream_t);
 
 template <int P>
 cudaError_t launch_adjoint(const DevTables& T, const DevState& S, const AdjState& A, double dt, cudaStream_t st) {

@@ -291,3 +291,31 @@ def test_window_on_a_side_stream_matches_default_stream():
         assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
     m1.close()
     m0.close()
+
+
+@pytest.mark.parametrize("n,nr,p", [(4, 3, 2), (4, 3, 3), (3, 5, 4)])
+def test_reverse_sweep_with_stored_iterates_matches_recompute(n, nr, p):
+    """geo_step_adjoint with a team schedule stores the checkpoint predictor's
+    Picard iterates in its forward recompute and the reverse team reads them;
+    with one thread per zone the reverse predictor recomputes them.  Both give
+    the same transpose of the step: gradients equal to rounding."""
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    o, m, U0, phi = setup_case(n, nr, p)
+    rng = np.random.default_rng(23 + p)
+    U = np.ascontiguousarray((U0 * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, U0.shape))).T)
+    dt = o.cfl_dt(U.T, 0.4)
+    Ut = torch.from_numpy(U).cuda()
+    pt = torch.from_numpy(phi.copy()).cuda()
+    gUo = torch.from_numpy(rng.standard_normal(U.shape)).cuda()
+    gpo = torch.from_numpy(rng.standard_normal(phi.shape)).cuda()
+    out = []
+    for sched in (geomhd.GEO_PRED_NODE_TEAM, geomhd.GEO_PRED_ZONE_THREAD):
+        geomhd.geo_set_predictor(m.h, sched)
+        gU, gp = torch.empty_like(Ut), torch.empty_like(pt)
+        geomhd.geo_step_adjoint(m.h, dt, Ut, pt, gUo, gpo, gU, gp)
+        torch.cuda.synchronize()
+        out.append((gU.cpu().numpy(), gp.cpu().numpy()))
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    m.close()
