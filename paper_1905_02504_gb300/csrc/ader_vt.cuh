@@ -229,11 +229,12 @@ __device__ __forceinline__ void vt_traces_group(int g, const R* XFz, int v, cons
   }
 }
 
-// resident blocks per SM (the register budget per thread follows); FP32 at p = 3:
-// 5 blocks (80 registers) measured 0.851 -> 0.770 ms against 4 on 196,608 zones
+// resident blocks per SM (the register budget per thread follows); FP32 at p = 3,
+// 196,608 zones: 4 / 5 / 6 blocks 0.851 / 0.770 / 0.719 ms; FP32 at p = 4,
+// 1,572,864 zones: 4 / 5 blocks 26.1 / 28.3 ms
 template <int P, typename R> struct VtOcc;
 template <> struct VtOcc<2, float> { static constexpr int MINB = 8; };
-template <> struct VtOcc<3, float> { static constexpr int MINB = 5; };
+template <> struct VtOcc<3, float> { static constexpr int MINB = 6; };
 template <> struct VtOcc<4, float> { static constexpr int MINB = 4; };
 template <> struct VtOcc<2, double> { static constexpr int MINB = 4; };
 template <> struct VtOcc<3, double> { static constexpr int MINB = 2; };
