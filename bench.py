@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--predictor", type=int, default=None, choices=[0, 1, 2],
                     help="predictor schedule: 0 one thread per zone, 1 one thread per node, 2 the node team "
                          "with the contraction in the variable layout (default: the library's)")
+    ap.add_argument("--prism", action="store_true",
+                    help="time the ADER-CG predictor on the paper's prism zones (geo_prism_predictor) on "
+                         "--prism-zones seeded synthetic frustums at --order")
+    ap.add_argument("--prism-zones", type=int, default=1 << 20)
     ap.add_argument("--contraction", action="store_true",
                     help="time the predictor's derivative contraction alone (FP32, CUDA-core and tensor-core "
                          "forms) beside the FP32-bulk predictor kernel on the same workload")
@@ -808,10 +812,60 @@ def contraction_arm(a):
     mesh.close()
 
 
+def prism_arm(a):
+    """The predictor on the paper's prism zones, alone: seeded synthetic frustums
+    (each zone the reference prism under its own random affine map, scaled to a
+    zone of a 1-2 radius shell), a smooth state with 1 % seeded noise at the
+    nodes, FP64.  Inputs and outputs (several GB) exceed L2; CUDA events on the
+    launching stream around each launch, after 3 warm-up launches."""
+    import numpy as np
+    import torch
+    from paper_1905_02504_gb300 import geomhd
+    torch.cuda.set_device(0)
+    p, Z = a.order, a.prism_zones
+    xi = geomhd.geo_prism_nodes(p)                               # (N, 3)
+    N = len(xi)
+    rng = np.random.default_rng(1905)
+    cen = rng.normal(size=(Z, 3))
+    cen *= (1.0 + rng.uniform(size=(Z, 1))) / np.linalg.norm(cen, axis=1, keepdims=True)
+    A = 0.02 * (np.eye(3)[None] + 0.1 * rng.standard_normal((Z, 3, 3)))
+    X = cen[:, None, :] + np.einsum("zde,ne->znd", A, xi)         # (Z, N, 3)
+    g = 5.0 / 3.0
+    U = np.empty((Z, N, 8))
+    U[..., 0] = 1.0 + 0.01 * rng.uniform(-1.0, 1.0, (Z, N))
+    U[..., 1:4] = U[..., :1] * np.array([0.3, -0.2, 0.1])
+    U[..., 5:8] = np.array([0.4, -0.3, 0.2])
+    U[..., 4] = 0.8 / (g - 1) + 0.5 * (U[..., 1:4] ** 2).sum(-1) / U[..., 0] + 0.5 * (U[..., 5:8] ** 2).sum(-1)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.transpose(2, 1, 0))).cuda()
+    Ud = torch.from_numpy(np.ascontiguousarray(U.transpose(2, 1, 0))).cuda()
+    del X, U
+    Uh = torch.empty((p, 8, N, Z), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            geomhd.geo_prism_predictor(p, Xd, Ud, 1e-3, g, Uh, stream.cuda_stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            geomhd.geo_prism_predictor(p, Xd, Ud, 1e-3, g, Uh, stream.cuda_stream)
+            e1.record(stream)
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t = float(np.median(ms))
+    ok = bool(torch.isfinite(Uh).all().item())
+    print(json.dumps({"study": "ADER-CG predictor on the paper's prism zones (geo_prism_predictor), FP64",
+                      "order": p, "nodes_per_zone": N, "zones": Z, "launches": a.steps, "ms_median": round(t, 4),
+                      "ms_min": round(min(ms), 4), "zones_per_s": Z / (t * 1e-3), "finite": ok,
+                      "inputs": "seeded affine prisms in a 1-2 shell, smooth state with 1 % noise; "
+                                "inputs and outputs larger than L2"}), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+    elif a.prism:
+        prism_arm(a)
     elif a.contraction:
         contraction_arm(a)
     elif a.convergence:

@@ -249,6 +249,32 @@ int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s);
  * zones exceeds 2^28.  Not part of geo_step. */
 int geo_probe_contraction(geo_mesh_t mesh, int tensor, int64_t zones, int reps, float* out_dev, float* ms);
 
+/* The ADER-CG predictor on the paper's own zones (Sec. V, Eqs. 5.12-5.14 and
+ * C.34-C.36): triangular-prism frustums mapped isoparametrically from the
+ * reference prism with unit edges and centroid at the origin, order 2, 3 or 4
+ * (N = 6 / 15 / 26 serendipity nodes, M = order time levels), FP64.  Per zone the
+ * metric terms at the nodes come from the node positions (h_alpha = D^alpha x,
+ * J = (h_xi x h_eta) . h_zeta, S^alpha the cofactor vectors), level 1 is J U, and
+ * `order` Picard iterations give the space-time nodal solution; the flux
+ * difference subtracts the geometric-conservation residual F . sum D^alpha S^alpha,
+ * so a uniform state stays uniform.  Device buffers, caller-owned, zone fastest:
+ * X_dev [3][N][zones] node positions, U_dev [8][N][zones] conserved variables at
+ * the nodes, Uh_dev [M][8][N][zones] the result (J times the conserved state at
+ * node i and time level tau_m: tau_1 = 0, then the Gauss points).  Node order as
+ * geo_prism_nodes.  Enqueued on `stream` (0 = legacy default), no
+ * synchronisation; the reference tables (< 20 KB per order) are built and copied
+ * to the device on the first call of each order and kept until exit.
+ * GEO_ERR_ARG for a bad order, zone count, null pointer, dt <= 0 or gamma <= 1. */
+int geo_prism_predictor(int order, int64_t zones, const double* X_dev, const double* U_dev, double dt, double gamma,
+                        double* Uh_dev, void* stream);
+
+/* Reference coordinates (xi, eta, zeta) of the order's prism nodes, [N][3] in
+ * host memory (count = doubles the buffer holds): the 6 vertices (top face
+ * zeta = +1/2 first), order - 2 equidistant nodes inside each of the 9 edges (the
+ * three sides of the top face, of the bottom face, then the three edges along
+ * zeta), and at order 4 the two triangle-face centroids (Fig. 7). */
+int geo_prism_nodes(int order, double* nodes, int64_t count);
+
 /* Copy one internal work buffer of the last step to host memory, for stage-by-
  * stage verification: which = 0 WENO-AO Taylor coefficients [8][NC1][Z],
  * 1 nodal normal B per face [NQmax][F], 2 predictor states at face points

@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -798,6 +799,65 @@ int geo_probe_fma_peak(int prec, void* stream, double* flops_per_s) {
   if (!flops_per_s) return fail(GEO_ERR_ARG, "bad arguments");
   cudaError_t e = geo::probe_fma(prec, static_cast<cudaStream_t>(stream), flops_per_s);
   if (e != cudaSuccess) return cuda_fail(e, "fma probe");
+  return GEO_OK;
+}
+
+// prism tables per order on the device, built on first use and kept until exit
+namespace {
+struct PrismTables {
+  std::once_flag once;
+  int status = GEO_ERR_CUDA;
+  std::string err;
+  int N = 0;
+  std::vector<double> nodes;
+  double* D = nullptr;  // [3][N][N]
+  double* R = nullptr;  // [M][M]
+};
+PrismTables g_prism[3];
+
+PrismTables& prism_tables_for(int p) {
+  PrismTables& P = g_prism[p - 2];
+  std::call_once(P.once, [&]() {
+    std::vector<double> D, wt, R;
+    if (!geo::prism_element(p, P.nodes, D)) {
+      P.status = GEO_ERR_ARG;
+      P.err = "prism element: singular basis";
+      return;
+    }
+    geo::time_tables(p, wt, R);
+    P.N = static_cast<int>(P.nodes.size() / 3);
+    cudaError_t e = cudaMalloc(&P.D, D.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&P.R, R.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(P.D, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P.R, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      P.err = std::string("prism tables: ") + cudaGetErrorString(e);
+      return;
+    }
+    P.status = GEO_OK;
+  });
+  return P;
+}
+}  // namespace
+
+int geo_prism_nodes(int order, double* nodes, int64_t count) {
+  if (order < 2 || order > 4 || !nodes) return fail(GEO_ERR_ARG, "geo_prism_nodes: bad arguments");
+  std::vector<double> n, D;
+  if (!geo::prism_element(order, n, D)) return fail(GEO_ERR_ARG, "geo_prism_nodes: singular basis");
+  if (count < static_cast<int64_t>(n.size())) return fail(GEO_ERR_ARG, "geo_prism_nodes: host buffer too small");
+  std::memcpy(nodes, n.data(), n.size() * sizeof(double));
+  return GEO_OK;
+}
+
+int geo_prism_predictor(int order, int64_t zones, const double* X_dev, const double* U_dev, double dt, double gamma,
+                        double* Uh_dev, void* stream) {
+  if (order < 2 || order > 4 || zones < 1 || !X_dev || !U_dev || !Uh_dev || !(dt > 0.0) || !(gamma > 1.0))
+    return fail(GEO_ERR_ARG, "geo_prism_predictor: bad arguments");
+  PrismTables& P = prism_tables_for(order);
+  if (P.status != GEO_OK) return fail(P.status, P.err);
+  cudaError_t e = geo::launch_prism_predictor_any(order, zones, P.D, P.R, X_dev, U_dev, dt, gamma, Uh_dev,
+                                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "geo_prism_predictor");
   return GEO_OK;
 }
 

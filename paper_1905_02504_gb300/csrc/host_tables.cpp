@@ -1032,50 +1032,7 @@ struct Builder {
     for (int ax = 0; ax < 3; ++ax)
       for (int i = 0; i < N; ++i) el.dbasis(el.nodes[i].data(), ax, &T.D[(static_cast<size_t>(ax) * N + i) * N]);
     // time: tau_1 = 0 and Gauss points; R = (K11)^-1 M1.
-    {
-      vector<double> xg, wg;
-      gauss_legendre(M - 1, xg, wg);
-      vector<double> tau(M);
-      tau[0] = 0.0;
-      for (int m = 1; m < M; ++m) tau[m] = 0.5 + xg[m - 1];
-      T.wt = wg;
-      auto phi = [&](int m, double t) {
-        double v = 1.0;
-        for (int l = 0; l < M; ++l)
-          if (l != m) v *= (t - tau[l]) / (tau[m] - tau[l]);
-        return v;
-      };
-      auto dphi = [&](int m, double t) {
-        double s = 0.0;
-        for (int l = 0; l < M; ++l) {
-          if (l == m) continue;
-          double v = 1.0 / (tau[m] - tau[l]);
-          for (int j = 0; j < M; ++j)
-            if (j != m && j != l) v *= (t - tau[j]) / (tau[m] - tau[j]);
-          s += v;
-        }
-        return s;
-      };
-      vector<double> xq, wq;
-      gauss_legendre(M + 1, xq, wq);
-      int nb = M - 1;
-      vector<double> K11(static_cast<size_t>(nb) * nb, 0.0), Mm(static_cast<size_t>(nb) * M, 0.0);
-      for (size_t g = 0; g < xq.size(); ++g) {
-        double t = 0.5 + xq[g];
-        for (int b = 1; b < M; ++b) {
-          for (int m = 1; m < M; ++m) K11[(b - 1) * nb + (m - 1)] += wq[g] * phi(b, t) * dphi(m, t);
-          for (int m = 0; m < M; ++m) Mm[(b - 1) * M + m] += wq[g] * phi(b, t) * phi(m, t);
-        }
-      }
-      invert_inplace(K11, nb);
-      T.R.assign(static_cast<size_t>(M) * M, 0.0);
-      for (int b = 0; b < nb; ++b)
-        for (int m = 0; m < M; ++m) {
-          double s = 0.0;
-          for (int j = 0; j < nb; ++j) s += K11[b * nb + j] * Mm[j * M + m];
-          T.R[(b + 1) * M + m] = s;
-        }
-    }
+    time_tables(M, T.wt, T.R);
     T.foff.assign(7, 0);
     for (int lf = 0; lf < 6; ++lf) T.foff[lf + 1] = T.foff[lf] + (lf >= 4 ? d.NQR : d.NQS);
     T.psiF.assign(static_cast<size_t>(NQT) * N, 0.0);
@@ -1169,6 +1126,118 @@ struct Builder {
     return "";
   }
 };
+
+// ---------------------------------------------------------------------------
+// the paper's reference triangular prism (Sec. V.c)
+// ---------------------------------------------------------------------------
+// monomials xi^a eta^b zeta^c of the order-p prism space (Eqs. 5.12-5.14)
+static const int PRISM_EXP2[6][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 0, 1}, {0, 1, 1}};
+static const int PRISM_EXP3[15][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2},
+                                      {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}, {2, 0, 1}, {0, 2, 1}, {1, 0, 2},
+                                      {0, 1, 2}};
+static const int PRISM_EXP4[26][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2},
+                                      {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0},
+                                      {2, 0, 1}, {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}, {1, 0, 3},
+                                      {0, 1, 3}, {3, 0, 1}, {0, 3, 1}, {2, 1, 1}, {1, 2, 1}};
+
+static double ipow(double x, int e) {
+  double r = 1.0;
+  for (int k = 0; k < e; ++k) r *= x;
+  return r;
+}
+
+bool prism_element(int p, vector<double>& nodes, vector<double>& D) {
+  if (p < 2 || p > 4) return false;
+  const int N = p == 2 ? 6 : (p == 3 ? 15 : 26);
+  const int(*ex)[3] = p == 2 ? PRISM_EXP2 : (p == 3 ? PRISM_EXP3 : PRISM_EXP4);
+  const double s3 = std::sqrt(3.0);
+  const double tri[3][2] = {{-0.5, -0.5 / s3}, {0.5, -0.5 / s3}, {0.0, 1.0 / s3}};
+  nodes.clear();
+  for (double z : {0.5, -0.5})
+    for (int v = 0; v < 3; ++v) nodes.insert(nodes.end(), {tri[v][0], tri[v][1], z});
+  // edges: the three sides of the top face, of the bottom face, then the three
+  // edges along zeta; p-2 equidistant interior nodes each
+  for (int e = 0; e < 9; ++e)
+    for (int k = 1; k <= p - 2; ++k) {
+      const double t = static_cast<double>(k) / (p - 1);
+      if (e < 6) {
+        const int a = e % 3, b = (e + 1) % 3;
+        const double z = e < 3 ? 0.5 : -0.5;
+        nodes.insert(nodes.end(), {(1 - t) * tri[a][0] + t * tri[b][0], (1 - t) * tri[a][1] + t * tri[b][1], z});
+      } else {
+        nodes.insert(nodes.end(), {tri[e - 6][0], tri[e - 6][1], 0.5 - t});
+      }
+    }
+  if (p == 4) nodes.insert(nodes.end(), {0.0, 0.0, 0.5, 0.0, 0.0, -0.5});
+  if (static_cast<int>(nodes.size()) != 3 * N) return false;
+  // Lagrange basis (Eq. 5.3): C = V^-1 with V_im = monomial m at node i
+  vector<double> V(static_cast<size_t>(N) * N);
+  for (int i = 0; i < N; ++i)
+    for (int m = 0; m < N; ++m)
+      V[i * N + m] = ipow(nodes[3 * i], ex[m][0]) * ipow(nodes[3 * i + 1], ex[m][1]) * ipow(nodes[3 * i + 2], ex[m][2]);
+  if (!invert_inplace(V, N)) return false;
+  D.assign(static_cast<size_t>(3) * N * N, 0.0);
+  for (int ax = 0; ax < 3; ++ax)
+    for (int i = 0; i < N; ++i)
+      for (int m = 0; m < N; ++m) {
+        const int e = ex[m][ax];
+        if (e == 0) continue;
+        int f[3] = {ex[m][0], ex[m][1], ex[m][2]};
+        f[ax] -= 1;
+        const double dm =
+            e * ipow(nodes[3 * i], f[0]) * ipow(nodes[3 * i + 1], f[1]) * ipow(nodes[3 * i + 2], f[2]);
+        for (int j = 0; j < N; ++j) D[(static_cast<size_t>(ax) * N + i) * N + j] += dm * V[m * N + j];
+      }
+  return true;
+}
+
+// Time tables of the ADER-CG predictor (Eqs. 5.15-5.17, 5.24-5.29): tau_1 = 0
+// and the M-1 Gauss points in [0, 1]; wt = their Gauss weights; R = (K11)^-1 M1
+// ([M][M], row 1 zero), with K11_bm = int phi_b phi_m' and M1_bm = int phi_b phi_m.
+void time_tables(int M, vector<double>& wt, vector<double>& R) {
+  vector<double> xg, wg;
+  gauss_legendre(M - 1, xg, wg);
+  vector<double> tau(M);
+  tau[0] = 0.0;
+  for (int m = 1; m < M; ++m) tau[m] = 0.5 + xg[m - 1];
+  wt = wg;
+  auto phi = [&](int m, double t) {
+    double v = 1.0;
+    for (int l = 0; l < M; ++l)
+      if (l != m) v *= (t - tau[l]) / (tau[m] - tau[l]);
+    return v;
+  };
+  auto dphi = [&](int m, double t) {
+    double s = 0.0;
+    for (int l = 0; l < M; ++l) {
+      if (l == m) continue;
+      double v = 1.0 / (tau[m] - tau[l]);
+      for (int j = 0; j < M; ++j)
+        if (j != m && j != l) v *= (t - tau[j]) / (tau[m] - tau[j]);
+      s += v;
+    }
+    return s;
+  };
+  vector<double> xq, wq;
+  gauss_legendre(M + 1, xq, wq);
+  int nb = M - 1;
+  vector<double> K11(static_cast<size_t>(nb) * nb, 0.0), Mm(static_cast<size_t>(nb) * M, 0.0);
+  for (size_t g = 0; g < xq.size(); ++g) {
+    double t = 0.5 + xq[g];
+    for (int b = 1; b < M; ++b) {
+      for (int m = 1; m < M; ++m) K11[(b - 1) * nb + (m - 1)] += wq[g] * phi(b, t) * dphi(m, t);
+      for (int m = 0; m < M; ++m) Mm[(b - 1) * M + m] += wq[g] * phi(b, t) * phi(m, t);
+    }
+  }
+  invert_inplace(K11, nb);
+  R.assign(static_cast<size_t>(M) * M, 0.0);
+  for (int b = 0; b < nb; ++b)
+    for (int m = 0; m < M; ++m) {
+      double s = 0.0;
+      for (int j = 0; j < nb; ++j) s += K11[b * nb + j] * Mm[j * M + m];
+      R[(b + 1) * M + m] = s;
+    }
+}
 
 std::string build_tables(int n, int nr, double r_in, double r_out, int p, Tables& T) {
   if (p < 2 || p > 4) return "order must be 2, 3 or 4";

@@ -107,6 +107,18 @@ struct Tables {
 // Builds every table.  Returns an empty string on success, else a message.
 std::string build_tables(int n, int nr, double r_in, double r_out, int p, Tables& T);
 
+// Time tables of the ADER-CG predictor (Eqs. 5.15-5.17, 5.24-5.29): wt = Gauss
+// weights of the M-1 Gauss times, R = (K11)^-1 M1 ([M][M], row 1 zero).
+void time_tables(int M, std::vector<double>& wt, std::vector<double>& R);
+
+// The paper's reference triangular prism (unit edges, centroid at the origin;
+// Sec. V.c, Eqs. 5.12-5.14, Fig. 7) at order p = 2, 3, 4: N = 6 / 15 / 26 nodes
+// ([N][3]: the 6 vertices, top face zeta = +1/2 first, then p-2 equidistant nodes
+// inside each of the 9 edges, then at p = 4 the two triangle-face centroids) and
+// D ([3][N][N]): D^alpha_ij = d psi_j / d xi_alpha at node i.  Returns false if
+// p is out of range or the Vandermonde matrix is singular.
+bool prism_element(int p, std::vector<double>& nodes, std::vector<double>& D);
+
 // Host geometry services for initial data.
 void zone_cubature(const Tables& T, int nq, double* pts, double* w);
 void edge_quadrature(const Tables& T, int nq, double* pts, double* tw);

@@ -1710,5 +1710,6 @@ cudaError_t probe_fma(int prec, cudaStream_t st, double* flops_per_s) {
 }
 
 #include "probe_contract.inc"
+#include "prism.inc"
 
 }  // namespace geo

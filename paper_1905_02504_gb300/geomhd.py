@@ -61,6 +61,8 @@ _SIGS = {
     "geo_stage_flops": [_h, _vp, _vp],
     "geo_probe_fma_peak": [ctypes.c_int, _vp, _pd],
     "geo_probe_contraction": [_h, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_float)],
+    "geo_prism_predictor": [ctypes.c_int, _i64, _vp, _vp, _d, _d, _vp, _vp],
+    "geo_prism_nodes": [ctypes.c_int, _vp, _i64],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_set_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_run_stage": [_h, ctypes.c_int, _d],
@@ -251,6 +253,23 @@ def geo_probe_fma_peak(prec=GEO_FP64, stream=0):
     v = _d()
     _check(_lib.geo_probe_fma_peak(prec, _vp(stream), ctypes.byref(v)), "geo_probe_fma_peak")
     return v.value
+
+
+def geo_prism_nodes(order):
+    """Reference coordinates of the order's prism nodes, (N, 3)."""
+    n = {2: 6, 3: 15, 4: 26}[order]
+    out = np.empty((n, 3))
+    _check(_lib.geo_prism_nodes(order, _ptr(out), out.size), "geo_prism_nodes")
+    return out
+
+
+def geo_prism_predictor(order, X, U, dt, gamma, Uh, stream=0):
+    """X [3][N][Z], U [8][N][Z], Uh [M][8][N][Z]: float64 CUDA tensors."""
+    for t in (X, U, Uh):
+        assert _is_device(t)
+    Z = X.shape[-1]
+    _check(_lib.geo_prism_predictor(order, Z, _ptr(X), _ptr(U), dt, gamma, _ptr(Uh), _vp(stream)),
+           "geo_prism_predictor")
 
 
 def geo_probe_contraction(h, tensor, zones, reps, out):
