@@ -810,8 +810,9 @@ struct PrismTables {
   std::string err;
   int N = 0;
   std::vector<double> nodes;
-  double* D = nullptr;  // [3][N][N]
-  double* R = nullptr;  // [M][M]
+  double* Dv = nullptr;         // [3][N][RL] nonzeros of each row of D^alpha
+  unsigned char* Dc = nullptr;  // [3][N][RL] their columns (padding: value 0, the row's own column)
+  double* R = nullptr;          // [M][M]
 };
 PrismTables g_prism[3];
 
@@ -825,10 +826,32 @@ PrismTables& prism_tables_for(int p) {
       return;
     }
     geo::time_tables(p, wt, R);
-    P.N = static_cast<int>(P.nodes.size() / 3);
-    cudaError_t e = cudaMalloc(&P.D, D.size() * sizeof(double));
+    const int N = static_cast<int>(P.nodes.size() / 3), RL = geo::prism_rl(p);
+    P.N = N;
+    std::vector<double> Dv(static_cast<size_t>(3) * N * RL, 0.0);
+    std::vector<unsigned char> Dc(static_cast<size_t>(3) * N * RL, 0);
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < N; ++i) {
+        int r = 0;
+        for (int j = 0; j < N; ++j) {
+          const double d = D[(static_cast<size_t>(a) * N + i) * N + j];
+          if (d == 0.0) continue;
+          if (r == RL) {
+            P.status = GEO_ERR_ARG;
+            P.err = "prism element: a row of D has more nonzeros than the row form holds";
+            return;
+          }
+          Dv[(static_cast<size_t>(a) * N + i) * RL + r] = d;
+          Dc[(static_cast<size_t>(a) * N + i) * RL + r] = static_cast<unsigned char>(j);
+          ++r;
+        }
+        for (; r < RL; ++r) Dc[(static_cast<size_t>(a) * N + i) * RL + r] = static_cast<unsigned char>(i);
+      }
+    cudaError_t e = cudaMalloc(&P.Dv, Dv.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&P.Dc, Dc.size());
     if (e == cudaSuccess) e = cudaMalloc(&P.R, R.size() * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemcpy(P.D, D.data(), D.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P.Dv, Dv.data(), Dv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P.Dc, Dc.data(), Dc.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P.R, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       P.err = std::string("prism tables: ") + cudaGetErrorString(e);
@@ -855,7 +878,7 @@ int geo_prism_predictor(int order, int64_t zones, const double* X_dev, const dou
     return fail(GEO_ERR_ARG, "geo_prism_predictor: bad arguments");
   PrismTables& P = prism_tables_for(order);
   if (P.status != GEO_OK) return fail(P.status, P.err);
-  cudaError_t e = geo::launch_prism_predictor_any(order, zones, P.D, P.R, X_dev, U_dev, dt, gamma, Uh_dev,
+  cudaError_t e = geo::launch_prism_predictor_any(order, zones, P.Dv, P.Dc, P.R, X_dev, U_dev, dt, gamma, Uh_dev,
                                                   static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "geo_prism_predictor");
   return GEO_OK;
