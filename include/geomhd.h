@@ -275,6 +275,13 @@ int geo_prism_predictor(int order, int64_t zones, const double* X_dev, const dou
  * zeta), and at order 4 the two triangle-face centroids (Fig. 7). */
 int geo_prism_nodes(int order, double* nodes, int64_t count);
 
+/* The order's prism derivative matrices as geo_prism_predictor uses them:
+ * D [3][N][N] host memory, D^alpha_ij = d psi_j / d xi_alpha at node i (Eq. 5.3
+ * basis on the monomials of Eqs. 5.12-5.14, nodes as geo_prism_nodes), with the
+ * entries that vanish exactly set to zero (the inverse leaves them at rounding
+ * level).  count = doubles the buffer holds. */
+int geo_prism_derivatives(int order, double* D, int64_t count);
+
 /* Copy one internal work buffer of the last step to host memory, for stage-by-
  * stage verification: which = 0 WENO-AO Taylor coefficients [8][NC1][Z],
  * 1 nodal normal B per face [NQmax][F], 2 predictor states at face points

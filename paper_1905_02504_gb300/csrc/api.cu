@@ -872,6 +872,15 @@ int geo_prism_nodes(int order, double* nodes, int64_t count) {
   return GEO_OK;
 }
 
+int geo_prism_derivatives(int order, double* D, int64_t count) {
+  if (order < 2 || order > 4 || !D) return fail(GEO_ERR_ARG, "geo_prism_derivatives: bad arguments");
+  std::vector<double> n, d;
+  if (!geo::prism_element(order, n, d)) return fail(GEO_ERR_ARG, "geo_prism_derivatives: singular basis");
+  if (count < static_cast<int64_t>(d.size())) return fail(GEO_ERR_ARG, "geo_prism_derivatives: host buffer too small");
+  std::memcpy(D, d.data(), d.size() * sizeof(double));
+  return GEO_OK;
+}
+
 int geo_prism_predictor(int order, int64_t zones, const double* X_dev, const double* U_dev, double dt, double gamma,
                         double* Uh_dev, void* stream) {
   if (order < 2 || order > 4 || zones < 1 || !X_dev || !U_dev || !Uh_dev || !(dt > 0.0) || !(gamma > 1.0))

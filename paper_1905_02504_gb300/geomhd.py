@@ -63,6 +63,7 @@ _SIGS = {
     "geo_probe_contraction": [_h, ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_float)],
     "geo_prism_predictor": [ctypes.c_int, _i64, _vp, _vp, _d, _d, _vp, _vp],
     "geo_prism_nodes": [ctypes.c_int, _vp, _i64],
+    "geo_prism_derivatives": [ctypes.c_int, _vp, _i64],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_set_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_run_stage": [_h, ctypes.c_int, _d],
@@ -260,6 +261,14 @@ def geo_prism_nodes(order):
     n = {2: 6, 3: 15, 4: 26}[order]
     out = np.empty((n, 3))
     _check(_lib.geo_prism_nodes(order, _ptr(out), out.size), "geo_prism_nodes")
+    return out
+
+
+def geo_prism_derivatives(order):
+    """The prism's D^alpha, (3, N, N)."""
+    n = {2: 6, 3: 15, 4: 26}[order]
+    out = np.empty((3, n, n))
+    _check(_lib.geo_prism_derivatives(order, _ptr(out), out.size), "geo_prism_derivatives")
     return out
 
 
