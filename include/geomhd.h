@@ -282,6 +282,12 @@ int geo_prism_nodes(int order, double* nodes, int64_t count);
  * level).  count = doubles the buffer holds. */
 int geo_prism_derivatives(int order, double* D, int64_t count);
 
+/* The time-coupling matrix R of the ADER-CG predictor that every mesh and
+ * geo_prism_predictor use (Eqs. 5.24-5.29, C.35-C.36: U_k = U_1 - sum_m R_km dF_m,
+ * time levels tau_1 = 0 and the order-1 Gauss points of [0, 1]): R [M][M] in
+ * host memory with M = order, row 1 zero.  count = doubles the buffer holds. */
+int geo_time_matrix(int order, double* R, int64_t count);
+
 /* Copy one internal work buffer of the last step to host memory, for stage-by-
  * stage verification: which = 0 WENO-AO Taylor coefficients [8][NC1][Z],
  * 1 nodal normal B per face [NQmax][F], 2 predictor states at face points

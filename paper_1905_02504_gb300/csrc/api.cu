@@ -872,6 +872,15 @@ int geo_prism_nodes(int order, double* nodes, int64_t count) {
   return GEO_OK;
 }
 
+int geo_time_matrix(int order, double* R, int64_t count) {
+  if (order < 2 || order > 4 || !R) return fail(GEO_ERR_ARG, "geo_time_matrix: bad arguments");
+  if (count < static_cast<int64_t>(order) * order) return fail(GEO_ERR_ARG, "geo_time_matrix: host buffer too small");
+  std::vector<double> wt, r;
+  geo::time_tables(order, wt, r);
+  std::memcpy(R, r.data(), r.size() * sizeof(double));
+  return GEO_OK;
+}
+
 int geo_prism_derivatives(int order, double* D, int64_t count) {
   if (order < 2 || order > 4 || !D) return fail(GEO_ERR_ARG, "geo_prism_derivatives: bad arguments");
   std::vector<double> n, d;

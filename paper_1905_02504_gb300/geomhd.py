@@ -64,6 +64,7 @@ _SIGS = {
     "geo_prism_predictor": [ctypes.c_int, _i64, _vp, _vp, _d, _d, _vp, _vp],
     "geo_prism_nodes": [ctypes.c_int, _vp, _i64],
     "geo_prism_derivatives": [ctypes.c_int, _vp, _i64],
+    "geo_time_matrix": [ctypes.c_int, _vp, _i64],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_set_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_run_stage": [_h, ctypes.c_int, _d],
@@ -261,6 +262,13 @@ def geo_prism_nodes(order):
     n = {2: 6, 3: 15, 4: 26}[order]
     out = np.empty((n, 3))
     _check(_lib.geo_prism_nodes(order, _ptr(out), out.size), "geo_prism_nodes")
+    return out
+
+
+def geo_time_matrix(order):
+    """The predictor's R, (M, M) with M = order."""
+    out = np.empty((order, order))
+    _check(_lib.geo_time_matrix(order, _ptr(out), out.size), "geo_time_matrix")
     return out
 
 
