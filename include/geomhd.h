@@ -167,6 +167,14 @@ int geo_zone_geometry(geo_mesh_t mesh, double* centroid, double* volume);
  * zone, the six faces' signed normals sum to zero up to rounding. */
 int geo_face_geometry(geo_mesh_t mesh, double* area, double* normal);
 
+/* The same zone and face geometry (centroid [Z][3], volume [Z], area [F],
+ * area-weighted normal [F][3], host buffers) straight from the host tables of a
+ * mesh that is not created on the device: the tables geo_mesh_create builds
+ * (isoparametric zones, Sec. II.b), without a GPU.  zones / faces must equal the
+ * mesh's Z = 6 subdiv^2 nr and F; GEO_ERR_ARG otherwise or for a bad mesh. */
+int geo_host_geometry(int subdiv, int nr, double r_in, double r_out, int order, int64_t zones, int64_t faces,
+                      double* centroid, double* volume, double* area, double* normal);
+
 /* Upload / download the state.  on_device != 0: U and phi are device pointers
  * (stream-ordered copies); otherwise host pointers (the call synchronises). */
 int geo_state_upload(geo_mesh_t mesh, const double* U, const double* phi, int on_device);

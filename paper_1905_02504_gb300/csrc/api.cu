@@ -402,6 +402,21 @@ int geo_zone_geometry(geo_mesh_t m, double* xc, double* vol) {
   return GEO_OK;
 }
 
+int geo_host_geometry(int subdiv, int nr, double r_in, double r_out, int order, int64_t zones, int64_t faces,
+                      double* centroid, double* volume, double* area, double* normal) {
+  if (!centroid || !volume || !area || !normal) return fail(GEO_ERR_ARG, "geo_host_geometry: bad arguments");
+  if (subdiv < 1 || nr < 1 || !(r_in > 0.0) || !(r_out > r_in) || order < 2 || order > 4)
+    return fail(GEO_ERR_ARG, "geo_host_geometry: bad mesh");
+  geo::Tables T;
+  const std::string err = geo::build_tables(subdiv, nr, r_in, r_out, order, T);
+  if (!err.empty()) return fail(GEO_ERR_ARG, err);
+  if (zones != static_cast<int64_t>(T.Z) || faces != static_cast<int64_t>(T.F))
+    return fail(GEO_ERR_ARG, "geo_host_geometry: zones / faces do not match the mesh");
+  geo::zone_centroids(T, centroid, volume);
+  geo::face_geometry(T, area, normal);
+  return GEO_OK;
+}
+
 int geo_face_geometry(geo_mesh_t m, double* area, double* normal) {
   if (!m || !area || !normal) return fail(GEO_ERR_ARG, "bad arguments");
   geo::face_geometry(m->T, area, normal);

@@ -65,6 +65,7 @@ _SIGS = {
     "geo_prism_nodes": [ctypes.c_int, _vp, _i64],
     "geo_prism_derivatives": [ctypes.c_int, _vp, _i64],
     "geo_time_matrix": [ctypes.c_int, _vp, _i64],
+    "geo_host_geometry": [ctypes.c_int, ctypes.c_int, _d, _d, ctypes.c_int, _i64, _i64, _vp, _vp, _vp, _vp],
     "geo_debug_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_set_buffer": [_h, ctypes.c_int, _vp, _i64],
     "geo_debug_run_stage": [_h, ctypes.c_int, _d],
@@ -263,6 +264,15 @@ def geo_prism_nodes(order):
     out = np.empty((n, 3))
     _check(_lib.geo_prism_nodes(order, _ptr(out), out.size), "geo_prism_nodes")
     return out
+
+
+def geo_host_geometry(subdiv, nr, r_in, r_out, order, zones, faces):
+    """(centroid (Z, 3), volume (Z,), area (F,), normal (F, 3)) from the host tables."""
+    xc, vol = np.empty((zones, 3)), np.empty(zones)
+    area, nrm = np.empty(faces), np.empty((faces, 3))
+    _check(_lib.geo_host_geometry(subdiv, nr, r_in, r_out, order, zones, faces, _ptr(xc), _ptr(vol), _ptr(area),
+                                  _ptr(nrm)), "geo_host_geometry")
+    return xc, vol, area, nrm
 
 
 def geo_time_matrix(order):
